@@ -1,0 +1,224 @@
+/*
+ * acopf.h -- C ABI of the GB300 (sm_103a) SQP-ADMM solver for the AC optimal
+ * power flow problem of Li, Schanen and Kim, "GPU-Accelerated Sequential
+ * Quadratic Programming Algorithm for Solving ACOPF" (arXiv 2310.13143).
+ *
+ * The solver runs the trust-region SQP method of Algorithm 1 on the
+ * rectangular ACOPF (Sec. III-A, eq. acopf).  Each QP subproblem (eq. QPsub,
+ * with d_wR and d_wI eliminated as in Sec. III-C, eq. elim) is solved by the
+ * component-decomposed ADMM of Algorithm 2: generator updates (eq.
+ * gen_kernel), per-branch 4-variable QPs (eq. line_kernel, solved by an
+ * augmented Lagrangian with a projected Newton inner solver), bus updates
+ * (eq. bus_kernel, closed form) and multiplier updates (eq. multiplier),
+ * with the residual test of Sec. IV-B.  Every step runs in CUDA kernels.
+ *
+ * Conventions
+ *  - Every function returns acopf_status; ACOPF_OK is 0.  Nothing throws
+ *    across the ABI.  Non-convergence is not an error: it is reported in
+ *    acopf_residuals.result.
+ *  - Units are per unit on base_mva, angles in radians, costs per MW.
+ *  - Pointers marked "host" are read (or written) during the call only; the
+ *    caller keeps ownership.  Device memory is owned by the handle.
+ *  - Calls are asynchronous on the handle's stream except the acopf_get_*
+ *    functions, which synchronise that stream before they return.
+ *  - A handle is not thread-safe; calls on different handles are independent.
+ *  - No CPU fallback: without a usable CUDA device acopf_create fails with
+ *    ACOPF_ECUDA.
+ */
+#ifndef ACOPF_H
+#define ACOPF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct acopf_ctx* acopf_handle;
+
+typedef enum {
+  ACOPF_OK = 0,
+  ACOPF_EINVAL = 1,     /* invalid argument or grid data (message in acopf_last_error) */
+  ACOPF_ENOMEM = 2,     /* device or host allocation failed */
+  ACOPF_ECUDA = 3,      /* CUDA runtime error */
+  ACOPF_ETIMEOUT = 4,   /* a device-wide barrier of the ADMM kernel gave up waiting */
+  ACOPF_ENOTREADY = 5   /* the requested data does not exist yet (e.g. no QP built) */
+} acopf_status;
+
+typedef enum {
+  ACOPF_CONVERGED = 0,      /* primal and dual infeasibility <= tol */
+  ACOPF_MAXITER = 1,        /* SQP iteration limit reached */
+  ACOPF_STEP_TOO_SMALL = 2, /* accepted step below step_tol, or trust region below delta_min */
+  ACOPF_NONFINITE = 3,      /* a non-finite value appeared */
+  ACOPF_RUNNING = 4         /* no solve has finished for this instance */
+} acopf_result;
+
+enum { ACOPF_FP64 = 0, ACOPF_MIXED = 1 };
+
+/* One grid (Sec. III-A).  All pointers are host arrays read during
+ * acopf_create only.  Branch (i, j) runs from f[l] to t[l] (0-based bus
+ * indices).  tap and shift may be NULL (tap 1, shift 0).  rate <= 0 means no
+ * line limit; angmin <= -2pi or angmax >= 2pi means no angle limit.
+ * Exactly one bus must have bus_type 3 (reference); its angle is fixed at 0. */
+typedef struct {
+  int32_t nbus;
+  const int32_t* bus_type;
+  const double *pd, *qd, *gs, *bs, *vmin, *vmax;
+  int32_t nbranch;
+  const int32_t *f, *t;
+  const double *r, *x, *b, *rate, *angmin, *angmax, *tap, *shift;
+  int32_t ngen;
+  const int32_t* gbus;
+  const double *pmin, *pmax, *qmin, *qmax, *c2, *c1, *c0;
+  double base_mva;
+} acopf_grid;
+
+typedef struct {
+  int32_t precision;     /* ACOPF_FP64: ADMM sweep in FP64.  ACOPF_MIXED: ADMM state and
+                            component updates in FP32; QP build, residual norms, step
+                            acceptance and the iterate stay FP64 */
+  int32_t use_angle;     /* 1: angle-difference limits enter the line subproblems */
+  int32_t device;        /* CUDA device ordinal */
+  int32_t block_threads; /* threads per CTA of the ADMM kernel (0: default 256) */
+  int32_t ctas_per_sm;   /* resident CTAs per SM of the ADMM kernel (0: as many as fit) */
+} acopf_options;
+
+typedef struct {
+  double rho;            /* ADMM penalty for every coupling (Tables I-II: 2e4) */
+  double eps;            /* tolerance on the l_inf primal and dual residuals (Sec. IV-B) */
+  int32_t max_iter;      /* ADMM iteration limit per QP */
+  int32_t warm;          /* 0: every QP starts from d = 0, lambda = 0;  1: lambda (and the
+                            line multipliers) carry over from the previous QP */
+  double alm_beta;       /* augmented-Lagrangian penalty, as a multiple of max_i Q_ii */
+  double alm_tol;        /* line-limit feasibility/complementarity tolerance */
+  int32_t alm_max_outer; /* multiplier updates per line subproblem */
+  int32_t newton_max;    /* projected Newton steps per multiplier update */
+  int64_t spin_limit;    /* clock cycles a CTA waits at a device-wide barrier before giving up */
+} admm_options;
+
+typedef struct {
+  double mu;             /* l1 merit penalty (Sec. IV-A: 1e5) */
+  double tol;            /* primal and dual infeasibility tolerance */
+  double step_tol;       /* stop when an accepted step's l_inf norm is below this */
+  double delta0, delta_max, delta_min; /* trust region: initial, cap, failure threshold */
+  int32_t max_sqp;
+  admm_options admm;
+} sqp_options;
+
+typedef struct {         /* caller-allocated host arrays (NULL to skip one) */
+  double *pg, *qg;       /* ngen */
+  double *vm, *va;       /* nbus: sqrt(w), theta */
+  double *wr, *wi;       /* nbranch */
+  double obj;            /* objective at the returned point */
+} acopf_solution;
+
+typedef struct {
+  double primal;         /* l_inf of all constraint violations (p.u.) */
+  double dual;           /* l_inf of the projected Lagrangian gradient / max(1, ||grad f||_inf) */
+  double r_inf, s_inf;   /* last ADMM primal and dual residuals */
+  double obj;
+  double delta;          /* trust-region radius */
+  int32_t sqp_iter, admm_iter, accepted;
+  int32_t result;        /* acopf_result */
+} acopf_residuals;
+
+/* defaults: FP64, angle limits on, device 0; rho 2e4, eps 1e-4, 20000 ADMM
+ * iterations, warm 1; mu 1e5, tol 1e-4, delta0 1, delta_max 10, 30 SQP steps */
+void acopf_default_options(acopf_options* o);
+void admm_default_options(admm_options* o);
+void sqp_default_options(sqp_options* o);
+
+const char* acopf_status_string(acopf_status s);
+/* message of the handle's last error (or of the last failed acopf_create when h is NULL) */
+acopf_status acopf_last_error(acopf_handle h, char* buf, size_t n);
+
+/* Build the device model of ngrids independent instances (Sec. III-A): the
+ * branch admittances of the pi model, bus/branch/generator adjacency, and all
+ * solver state.  Instances are solved together by every later call.
+ * Errors: EINVAL for an index out of range, x <= 0 with r = 0, vmin > vmax,
+ * pmin > pmax, qmin > qmax, no (or more than one) reference bus, an isolated
+ * bus, or ngrids < 1; ECUDA without a device. */
+acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_options* opt,
+                          acopf_handle* out);
+acopf_status acopf_destroy(acopf_handle h);
+
+/* Stream (a cudaStream_t) on which all later work is queued; NULL = legacy default. */
+acopf_status acopf_set_stream(acopf_handle h, void* cuda_stream);
+
+/* Replace the loads of instance inst (host arrays of its nbus). */
+acopf_status acopf_set_loads(acopf_handle h, int32_t inst, const double* pd, const double* qd);
+
+/* Run Algorithm 1 from a flat start (or from the warm start set below) on
+ * every instance until each one converges or stops. */
+acopf_status sqp_solve(acopf_handle h, const sqp_options* o);
+
+/* One QP at the current iterate: build it (Alg. 1 line 6) and solve it by
+ * ADMM (Alg. 2); the step and the new multipliers become available through
+ * acopf_get_step.  The iterate itself is not changed. */
+acopf_status admm_solve_qp(acopf_handle h, double delta, const admm_options* o);
+
+/* Warm start of instance inst: x0 = NLP point in the layout of
+ * acopf_set_iterate (may be NULL), lambda0 = ADMM multipliers in the layout of
+ * acopf_get_admm_state (may be NULL), rho = per-component penalties
+ * (nbranch values, then ngen values; may be NULL).  Used by the next
+ * sqp_solve. */
+acopf_status acopf_set_warm_start(acopf_handle h, int32_t inst, const double* x0, const double* lambda0,
+                                  const double* rho);
+
+acopf_status acopf_get_solution(acopf_handle h, int32_t inst, acopf_solution* out);
+acopf_status acopf_get_residuals(acopf_handle h, int32_t inst, acopf_residuals* out);
+
+/* ---- lower-level calls used by the parity tests and the benchmark ------- */
+
+/* NLP point of instance inst, host, n = 2*ngen + 2*nbus + 2*nbranch values in
+ * the order [pg | qg | w | theta | wR | wI] (w = v^2), and the multipliers pi
+ * of eq. lag (4 per branch: pi11 pi12 pi13 pi14, branch-major; may be NULL). */
+acopf_status acopf_set_iterate(acopf_handle h, int32_t inst, const double* x, const double* pi);
+acopf_status acopf_get_iterate(acopf_handle h, int32_t inst, double* x, double* pi);
+
+/* Build the QP at the current iterate with trust-region radius delta and
+ * penalty rho (every coupling), without solving it. */
+acopf_status acopf_build_qp(acopf_handle h, double delta, double rho, int32_t use_angle);
+
+/* Host copies of the QP data of instance inst (any pointer may be NULL):
+ * per branch (branch-major): flow 4 (p_ij q_ij p_ji q_ji), H 36 (Hessian of
+ * L_ij over z = (w_i, th_i, wR, wI, w_j, th_j), row-major), aR 4, aI 4, bR 1,
+ * bI 1, QH 16 (A'HA), gH 4 (A'Hb), F 16 (flow-change rows over
+ * dbar = (d_wi, d_thi, d_wj, d_thj)), f0 4, lo 4, hi 4, G 8 (line-limit rows),
+ * grhs 2, alo 1, ahi 1; per generator: gen 6 (f', f'', lp, up, lq, uq);
+ * per bus: bus 2 (p_i^{d,(k)}, q_i^{d,(k)}). */
+typedef struct {
+  double *flow, *H, *aR, *aI, *bR, *bI, *QH, *gH, *F, *f0, *lo, *hi, *G, *grhs, *alo, *ahi;
+  double *gen, *bus;
+} acopf_qp_view;
+acopf_status acopf_get_qp(acopf_handle h, int32_t inst, acopf_qp_view* out);
+
+/* ADMM state of instance inst (host, any pointer may be NULL).  Couplings of
+ * branch l in the order p_ij q_ij p_ji q_ji w_i(ij) th_i(ij) w_j(ji) th_j(ji):
+ * x = line side, z = bus side, lam = multipliers (8 per branch); generators:
+ * xg, zg, lg (2 per generator: p, q); bus: zb (d_w, d_theta), nu (power-balance
+ * multipliers), 2 per bus; ul: line inequality multipliers (lim_ij, lim_ji,
+ * ang_hi, ang_lo), 4 per branch. */
+typedef struct {
+  double *x, *z, *lam, *xg, *zg, *lg, *zb, *nu, *ul;
+} acopf_admm_state;
+acopf_status acopf_get_admm_state(acopf_handle h, int32_t inst, acopf_admm_state* out);
+acopf_status acopf_set_admm_state(acopf_handle h, int32_t inst, const acopf_admm_state* in);
+
+/* Run exactly n ADMM iterations (n >= 1) of Alg. 2 on the QP last built, from
+ * the current ADMM state, ignoring the residual test (o->eps unused). */
+acopf_status admm_iterate(acopf_handle h, int32_t n, const admm_options* o);
+
+/* Step d of the last QP (layout of acopf_set_iterate: d_wR, d_wI from eq.
+ * elim on the bus values) and the multipliers pi recovered from the line
+ * subproblems' KKT conditions (Sec. IV-B), host arrays. */
+acopf_status acopf_get_step(acopf_handle h, int32_t inst, double* d, double* pi);
+
+/* Kernel launches issued by this handle since it was created. */
+acopf_status acopf_launch_count(acopf_handle h, int64_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACOPF_H */
