@@ -87,6 +87,9 @@ typedef struct {
 typedef struct {
   double rho;            /* ADMM penalty for every coupling (Tables I-II: 2e4) */
   double eps;            /* tolerance on the l_inf primal and dual residuals (Sec. IV-B) */
+  double eps_dual;       /* separate tolerance on the dual residual s (0: eps).  In the FP32
+                            sweep s = rho (z+ - z) has a floor of about rho times the FP32
+                            resolution of z, so the mixed path needs a larger value */
   int32_t max_iter;      /* ADMM iteration limit per QP */
   int32_t warm;          /* 0: every QP starts from d = 0, lambda = 0;  1: lambda (and the
                             line multipliers) carry over from the previous QP */
@@ -159,8 +162,9 @@ acopf_status sqp_solve(acopf_handle h, const sqp_options* o);
 acopf_status admm_solve_qp(acopf_handle h, double delta, const admm_options* o);
 
 /* Warm start of instance inst: x0 = NLP point in the layout of
- * acopf_set_iterate (may be NULL), lambda0 = ADMM multipliers in the layout of
- * acopf_get_admm_state (may be NULL), rho = per-component penalties
+ * acopf_set_iterate (may be NULL; pi is reset to 0), lambda0 = ADMM multipliers:
+ * the lam array of acopf_admm_state (8 per branch) followed by its lg array
+ * (2 per generator) (may be NULL), rho = per-component penalties
  * (nbranch values, then ngen values; may be NULL).  Used by the next
  * sqp_solve. */
 acopf_status acopf_set_warm_start(acopf_handle h, int32_t inst, const double* x0, const double* lambda0,
@@ -217,6 +221,15 @@ acopf_status acopf_get_step(acopf_handle h, int32_t inst, double* d, double* pi)
 
 /* Kernel launches issued by this handle since it was created. */
 acopf_status acopf_launch_count(acopf_handle h, int64_t* n);
+
+/* Device timing of the ADMM sweep kernel: with on = 1, CUDA events are
+ * recorded on the handle's stream around every sweep launch; the accumulated
+ * device milliseconds, the number of sweep launches and the ADMM iterations
+ * they ran (summed over instances' maximum per launch) are returned by
+ * acopf_get_profile, which synchronises the stream.  on = 0 stops recording;
+ * acopf_profile always resets the totals. */
+acopf_status acopf_profile(acopf_handle h, int32_t on);
+acopf_status acopf_get_profile(acopf_handle h, double* sweep_ms, int64_t* sweeps, int64_t* admm_iters);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,334 @@
+"""ctypes binding of libacopf.so (include/acopf.h).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  There is no CPU fallback -- if the library is missing or no
+CUDA device is usable the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libacopf.so")
+
+DP = C.POINTER(C.c_double)
+IP = C.POINTER(C.c_int32)
+
+ACOPF_FP64, ACOPF_MIXED = 0, 1
+RESULTS = {0: "converged", 1: "max_iter", 2: "step_too_small", 3: "non_finite", 4: "running"}
+STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTREADY"}
+
+
+class AcopfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class acopf_grid(C.Structure):
+    _fields_ = [("nbus", C.c_int32), ("bus_type", IP), ("pd", DP), ("qd", DP), ("gs", DP), ("bs", DP),
+                ("vmin", DP), ("vmax", DP), ("nbranch", C.c_int32), ("f", IP), ("t", IP), ("r", DP), ("x", DP),
+                ("b", DP), ("rate", DP), ("angmin", DP), ("angmax", DP), ("tap", DP), ("shift", DP),
+                ("ngen", C.c_int32), ("gbus", IP), ("pmin", DP), ("pmax", DP), ("qmin", DP), ("qmax", DP),
+                ("c2", DP), ("c1", DP), ("c0", DP), ("base_mva", C.c_double)]
+
+
+class acopf_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("use_angle", C.c_int32), ("device", C.c_int32),
+                ("block_threads", C.c_int32), ("ctas_per_sm", C.c_int32)]
+
+
+class admm_options(C.Structure):
+    _fields_ = [("rho", C.c_double), ("eps", C.c_double), ("eps_dual", C.c_double), ("max_iter", C.c_int32),
+                ("warm", C.c_int32),
+                ("alm_beta", C.c_double), ("alm_tol", C.c_double), ("alm_max_outer", C.c_int32),
+                ("newton_max", C.c_int32), ("spin_limit", C.c_int64)]
+
+
+class sqp_options(C.Structure):
+    _fields_ = [("mu", C.c_double), ("tol", C.c_double), ("step_tol", C.c_double), ("delta0", C.c_double),
+                ("delta_max", C.c_double), ("delta_min", C.c_double), ("max_sqp", C.c_int32),
+                ("admm", admm_options)]
+
+
+class acopf_solution(C.Structure):
+    _fields_ = [("pg", DP), ("qg", DP), ("vm", DP), ("va", DP), ("wr", DP), ("wi", DP), ("obj", C.c_double)]
+
+
+class acopf_residuals(C.Structure):
+    _fields_ = [("primal", C.c_double), ("dual", C.c_double), ("r_inf", C.c_double), ("s_inf", C.c_double),
+                ("obj", C.c_double), ("delta", C.c_double), ("sqp_iter", C.c_int32), ("admm_iter", C.c_int32),
+                ("accepted", C.c_int32), ("result", C.c_int32)]
+
+
+QP_FIELDS = [("flow", 4), ("H", 36), ("aR", 4), ("aI", 4), ("bR", 1), ("bI", 1), ("QH", 16), ("gH", 4),
+             ("F", 16), ("f0", 4), ("lo", 4), ("hi", 4), ("G", 8), ("grhs", 2), ("alo", 1), ("ahi", 1)]
+
+
+class acopf_qp_view(C.Structure):
+    _fields_ = [(n, DP) for n, _ in QP_FIELDS] + [("gen", DP), ("bus", DP)]
+
+
+STATE_FIELDS = [("x", 8, "L"), ("z", 8, "L"), ("lam", 8, "L"), ("xg", 2, "G"), ("zg", 2, "G"), ("lg", 2, "G"),
+                ("zb", 2, "B"), ("nu", 2, "B"), ("ul", 4, "L")]
+
+
+class acopf_admm_state(C.Structure):
+    _fields_ = [(n, DP) for n, _, _ in STATE_FIELDS]
+
+
+_lib = None
+
+
+def lib():
+    """Load libacopf.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2310_13143_gb300.build.build() first")
+        L = C.CDLL(LIB_PATH)
+        H = C.c_void_p
+        S = C.c_int
+        sig = {
+            "acopf_default_options": (None, [C.POINTER(acopf_options)]),
+            "admm_default_options": (None, [C.POINTER(admm_options)]),
+            "sqp_default_options": (None, [C.POINTER(sqp_options)]),
+            "acopf_status_string": (C.c_char_p, [S]),
+            "acopf_last_error": (S, [H, C.c_char_p, C.c_size_t]),
+            "acopf_create": (S, [C.POINTER(acopf_grid), C.c_int32, C.POINTER(acopf_options), C.POINTER(H)]),
+            "acopf_destroy": (S, [H]),
+            "acopf_set_stream": (S, [H, C.c_void_p]),
+            "acopf_set_loads": (S, [H, C.c_int32, DP, DP]),
+            "sqp_solve": (S, [H, C.POINTER(sqp_options)]),
+            "admm_solve_qp": (S, [H, C.c_double, C.POINTER(admm_options)]),
+            "acopf_set_warm_start": (S, [H, C.c_int32, DP, DP, DP]),
+            "acopf_get_solution": (S, [H, C.c_int32, C.POINTER(acopf_solution)]),
+            "acopf_get_residuals": (S, [H, C.c_int32, C.POINTER(acopf_residuals)]),
+            "acopf_set_iterate": (S, [H, C.c_int32, DP, DP]),
+            "acopf_get_iterate": (S, [H, C.c_int32, DP, DP]),
+            "acopf_build_qp": (S, [H, C.c_double, C.c_double, C.c_int32]),
+            "acopf_get_qp": (S, [H, C.c_int32, C.POINTER(acopf_qp_view)]),
+            "acopf_get_admm_state": (S, [H, C.c_int32, C.POINTER(acopf_admm_state)]),
+            "acopf_set_admm_state": (S, [H, C.c_int32, C.POINTER(acopf_admm_state)]),
+            "admm_iterate": (S, [H, C.c_int32, C.POINTER(admm_options)]),
+            "acopf_get_step": (S, [H, C.c_int32, DP, DP]),
+            "acopf_launch_count": (S, [H, C.POINTER(C.c_int64)]),
+            "acopf_profile": (S, [H, C.c_int32]),
+            "acopf_get_profile": (S, [H, DP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+EXPORTED = ["acopf_default_options", "admm_default_options", "sqp_default_options", "acopf_status_string",
+            "acopf_last_error", "acopf_create", "acopf_destroy", "acopf_set_stream", "acopf_set_loads", "sqp_solve",
+            "admm_solve_qp", "acopf_set_warm_start", "acopf_get_solution", "acopf_get_residuals",
+            "acopf_set_iterate", "acopf_get_iterate", "acopf_build_qp", "acopf_get_qp", "acopf_get_admm_state",
+            "acopf_set_admm_state", "admm_iterate", "acopf_get_step", "acopf_launch_count", "acopf_profile",
+            "acopf_get_profile"]
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(DP)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def default_admm(**kw) -> admm_options:
+    o = admm_options()
+    lib().admm_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def default_sqp(admm: dict | None = None, **kw) -> sqp_options:
+    o = sqp_options()
+    lib().sqp_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    for k, v in (admm or {}).items():
+        setattr(o.admm, k, v)
+    return o
+
+
+class Solver:
+    """A handle over one or more grids (``gridgen.Grid``-like objects)."""
+
+    def __init__(self, grids, precision: str = "fp64", use_angle: bool = True, device: int = 0,
+                 block_threads: int = 256, ctas_per_sm: int = 0):
+        if not isinstance(grids, (list, tuple)):
+            grids = [grids]
+        self.grids = list(grids)
+        self._keep = []
+        arr = (acopf_grid * len(grids))()
+        for k, g in enumerate(grids):
+            s = arr[k]
+            s.nbus, s.nbranch, s.ngen = g.nbus, g.nbranch, g.ngen
+            for name in ("pd", "qd", "gs", "bs", "vmin", "vmax", "r", "x", "b", "rate", "angmin", "angmax",
+                         "tap", "shift", "pmin", "pmax", "qmin", "qmax", "c2", "c1", "c0"):
+                a = _f64(getattr(g, name))
+                self._keep.append(a)
+                setattr(s, name, a.ctypes.data_as(DP))
+            for name in ("bus_type", "f", "t", "gbus"):
+                a = np.ascontiguousarray(getattr(g, name), dtype=np.int32)
+                self._keep.append(a)
+                setattr(s, name, a.ctypes.data_as(IP))
+            s.base_mva = float(g.base_mva)
+        o = acopf_options()
+        lib().acopf_default_options(C.byref(o))
+        o.precision = ACOPF_MIXED if precision == "mixed" else ACOPF_FP64
+        o.use_angle = int(bool(use_angle))
+        o.device = device
+        o.block_threads = block_threads
+        o.ctas_per_sm = ctas_per_sm
+        h = C.c_void_p()
+        st = lib().acopf_create(arr, len(grids), C.byref(o), C.byref(h))
+        if st != 0:
+            buf = C.create_string_buffer(512)
+            lib().acopf_last_error(None, buf, 512)
+            raise AcopfError(st, buf.value.decode())
+        self.h = h
+        self._keep_arr = arr
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().acopf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != 0:
+            buf = C.create_string_buffer(512)
+            lib().acopf_last_error(self.h, buf, 512)
+            raise AcopfError(st, buf.value.decode())
+
+    def _dims(self, inst):
+        g = self.grids[inst]
+        return g.nbus, g.nbranch, g.ngen
+
+    def nvars(self, inst=0):
+        B, L, G = self._dims(inst)
+        return 2 * G + 2 * B + 2 * L
+
+    # ------------------------------------------------------------ solver calls
+    def set_stream(self, stream_ptr: int):
+        self._check(lib().acopf_set_stream(self.h, C.c_void_p(stream_ptr)))
+
+    def set_loads(self, inst, pd, qd):
+        pd, qd = _f64(pd), _f64(qd)
+        self._check(lib().acopf_set_loads(self.h, inst, _dp(pd), _dp(qd)))
+
+    def sqp_solve(self, opts: sqp_options | None = None):
+        self._check(lib().sqp_solve(self.h, C.byref(opts or default_sqp())))
+
+    def admm_solve_qp(self, delta=1.0, opts: admm_options | None = None):
+        self._check(lib().admm_solve_qp(self.h, float(delta), C.byref(opts or default_admm())))
+
+    def admm_iterate(self, n, opts: admm_options | None = None):
+        self._check(lib().admm_iterate(self.h, int(n), C.byref(opts or default_admm())))
+
+    def build_qp(self, delta=1.0, rho=2e4, use_angle=True):
+        self._check(lib().acopf_build_qp(self.h, float(delta), float(rho), int(bool(use_angle))))
+
+    def set_warm_start(self, inst, x0=None, lambda0=None, rho=None):
+        a, b, c = (None if v is None else _f64(v) for v in (x0, lambda0, rho))
+        self._check(lib().acopf_set_warm_start(self.h, inst, _dp(a), _dp(b), _dp(c)))
+
+    # -------------------------------------------------------------- read-outs
+    def set_iterate(self, inst, x, pi=None):
+        x = _f64(x)
+        pi = None if pi is None else _f64(pi)
+        self._check(lib().acopf_set_iterate(self.h, inst, _dp(x), _dp(pi)))
+
+    def get_iterate(self, inst=0):
+        B, L, G = self._dims(inst)
+        x = np.zeros(2 * G + 2 * B + 2 * L)
+        pi = np.zeros(4 * max(L, 1))
+        self._check(lib().acopf_get_iterate(self.h, inst, _dp(x), _dp(pi)))
+        return x, pi[:4 * L]
+
+    def get_qp(self, inst=0):
+        B, L, G = self._dims(inst)
+        out = {n: np.zeros(w * max(L, 1)) for n, w in QP_FIELDS}
+        out["gen"] = np.zeros(6 * G)
+        out["bus"] = np.zeros(2 * B)
+        v = acopf_qp_view(**{n: _dp(a) for n, a in out.items()})
+        self._check(lib().acopf_get_qp(self.h, inst, C.byref(v)))
+        res = {}
+        for n, w in QP_FIELDS:
+            a = out[n][:w * L]
+            res[n] = a.reshape(L, w) if w > 1 else a
+        gen = out["gen"].reshape(G, 6)
+        for k, n in enumerate(("gd1", "gd2", "glp", "gup", "glq", "guq")):
+            res[n] = gen[:, k].copy()
+        res["pdk"] = out["bus"][0::2].copy()
+        res["qdk"] = out["bus"][1::2].copy()
+        return res
+
+    def get_admm_state(self, inst=0):
+        B, L, G = self._dims(inst)
+        cnt = {"L": max(L, 1), "G": G, "B": B}
+        out = {n: np.zeros(w * cnt[c]) for n, w, c in STATE_FIELDS}
+        s = acopf_admm_state(**{n: _dp(a) for n, a in out.items()})
+        self._check(lib().acopf_get_admm_state(self.h, inst, C.byref(s)))
+        real = {"L": L, "G": G, "B": B}
+        return {n: out[n][:w * real[c]].reshape(real[c], w) for n, w, c in STATE_FIELDS}
+
+    def set_admm_state(self, inst, state: dict):
+        arrs = {n: (None if state.get(n) is None else _f64(np.asarray(state[n]).ravel())) for n, _, _ in STATE_FIELDS}
+        s = acopf_admm_state(**{n: (_dp(a) if a is not None else None) for n, a in arrs.items()})
+        self._check(lib().acopf_set_admm_state(self.h, inst, C.byref(s)))
+
+    def get_step(self, inst=0):
+        B, L, G = self._dims(inst)
+        d = np.zeros(2 * G + 2 * B + 2 * L)
+        pi = np.zeros(4 * max(L, 1))
+        self._check(lib().acopf_get_step(self.h, inst, _dp(d), _dp(pi)))
+        return d, pi[:4 * L]
+
+    def get_solution(self, inst=0):
+        B, L, G = self._dims(inst)
+        arrs = {"pg": np.zeros(G), "qg": np.zeros(G), "vm": np.zeros(B), "va": np.zeros(B),
+                "wr": np.zeros(max(L, 1)), "wi": np.zeros(max(L, 1))}
+        s = acopf_solution(**{n: _dp(a) for n, a in arrs.items()})
+        self._check(lib().acopf_get_solution(self.h, inst, C.byref(s)))
+        arrs["wr"], arrs["wi"] = arrs["wr"][:L], arrs["wi"][:L]
+        arrs["obj"] = s.obj
+        return arrs
+
+    def get_residuals(self, inst=0):
+        r = acopf_residuals()
+        self._check(lib().acopf_get_residuals(self.h, inst, C.byref(r)))
+        d = {n: getattr(r, n) for n, _ in acopf_residuals._fields_}
+        d["result_name"] = RESULTS.get(d["result"], str(d["result"]))
+        return d
+
+    def profile(self, on=True):
+        self._check(lib().acopf_profile(self.h, int(bool(on))))
+
+    def get_profile(self):
+        ms = C.c_double()
+        n, it = C.c_int64(), C.c_int64()
+        self._check(lib().acopf_get_profile(self.h, C.byref(ms), C.byref(n), C.byref(it)))
+        return dict(sweep_ms=ms.value, sweeps=n.value, admm_iters=it.value)
+
+    def launch_count(self):
+        n = C.c_int64()
+        self._check(lib().acopf_launch_count(self.h, C.byref(n)))
+        return n.value

@@ -1,0 +1,162 @@
+// Internal layout of the GB300 SQP-ADMM solver (not part of the C ABI).
+//
+// All instances of a handle are concatenated: buses, branches and generators
+// carry global indices, and per-instance segments are given by *_off arrays.
+// Generators are stored sorted by bus (gen_ptr is the CSR row pointer of
+// "generators at bus i"); the user's generator order is restored on output.
+//
+// ADMM state is end-major: each branch has two ends (from = 0, to = 1) and
+// each end carries the four couplings (p, q, w, theta) of eq. cpl as one
+// 4-vector, so a bus touches one 16/32-byte vector per incident end and a
+// branch reads its 8 couplings as two contiguous vectors.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/acopf.h"
+
+namespace acopf {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double kBig = 1e30;
+
+// per-branch sweep record: 56 values in 14 chunks of 4, chunk c of branch l
+// stored at rec[c * L + l] (coalesced 16/32-byte loads across a warp)
+//   0-9   Q (packed upper triangle q00 q01 q02 q03 q11 q12 q13 q22 q23 q33)
+//   10-25 F (rows p_ij q_ij p_ji q_ji, columns dbar)
+//   26-29 f0        30-33 c0 = gH + rho F^T f0
+//   34-37 lo        38-41 hi
+//   42-49 line-limit rows, normalised to unit 2-norm
+//   50-51 their right-hand sides (normalised)
+//   52 alo  53 ahi  (angle-difference bounds on d_thi - d_thj; >= 1e29: none)
+//   54-55 2-norms of the two line-limit rows (0: row disabled)
+constexpr int kRecChunks = 14;
+
+template <typename T>
+struct alignas(4 * sizeof(T)) V4 {
+  T x, y, z, w;
+};
+template <typename T>
+struct alignas(2 * sizeof(T)) V2 {
+  T x, y;
+};
+
+struct InstCtl {            // per-instance SQP control, device resident
+  double delta, mu, tol, step_tol, delta_max, delta_min;
+  double obj, primal, dual, r_inf, s_inf;
+  double ared, pred, dnorm;
+  double rho, eps;
+  int32_t sqp_iter, admm_iter_total, admm_iter_last, accepted;
+  int32_t result;           // acopf_result
+  int32_t accept_last;
+  int32_t admm_done;        // 1 once the ADMM residual test passed in the last sweep
+  int32_t pad;
+};
+
+// raw device pointers shared by all kernels
+struct Dev {
+  int K, B, L, G;
+  int *bus_off, *br_off, *gen_off;
+  int *bus_inst, *br_inst, *gen_inst;
+  // buses
+  double *pd, *qd, *gs, *bs, *wmin, *wmax;
+  int* isref;
+  int *end_ptr, *end_idx, *gen_ptr;
+  // branches
+  int *f, *t;
+  double* Y;        // [8][L]: gii bii gij bij gji bji gjj bjj
+  double* s2;       // rate^2, or -1 (no limit)
+  double *angmin, *angmax;
+  // generators (sorted by bus)
+  int* gbus;
+  double *pmin, *pmax, *qmin, *qmax, *cq, *cl, *cc;  // cost = cq p^2 + cl p + cc (p in p.u.)
+  // iterate (FP64)
+  double *pg, *qg, *w, *th, *wr, *wi;
+  double* pi;       // [4][L]
+  // step (FP64) and recovered multipliers
+  double *dpg, *dqg, *dw, *dth, *dwr, *dwi;
+  double* pi_new;   // [4][L]
+  // QP data needed in FP64 after the sweep
+  double* flow;     // [4][L]
+  double *aR, *aI;  // [4][L]
+  double *bR, *bI;  // [L]
+  double *gd1, *gd2;
+  double* rho_l;    // [L] per-branch penalty (FP64 master copy)
+  double* rho_g;    // [G]
+  // sweep data and state in the sweep precision (float or double)
+  void* lrec;       // [14][L] chunks
+  void* grec;       // [2][G] chunks: (gd1, gd2, lp, up), (lq, uq, rho, 0)
+  void* brec;       // [B] chunk: (pdk, qdk, gs, bs)
+  void* trho_l;     // [L]
+  void *X, *Z, *LAM;  // V4 [2L]
+  void* U;            // V4 [L]
+  void *XG, *ZG, *LG; // V2 [G]
+  void *ZB, *NU;      // V2 [B]
+  // sweep control
+  unsigned long long* res_slots; // [2 slots][2 (r,s)][K]
+  int* admm_done;     // [K]
+  int* admm_iters;    // [K]
+  double* admm_rs;    // [2][K]
+  unsigned int* bar;  // [2]: count, generation
+  int* err;           // [1]
+  // merit / KKT scratch
+  double* flow_xd;    // [4][L]
+  double* tbr;        // [8][L]
+  double* tbus;       // [4][B]
+  double* tgen;       // [8][G]
+  double* dend;       // [2][2L] per-end gradient contributions (w, theta)
+  double* red;        // [16][K] per-instance reductions
+  InstCtl* ctl;       // [K]
+  int* n_running;     // [1]
+  // export buffers (allocated on demand)
+  double *xbr, *xgen, *xbus;
+};
+
+// host-side handle
+struct Ctx {
+  Dev d{};
+  int precision = ACOPF_FP64;
+  int use_angle = 1;
+  int device = 0;
+  int block_threads = 256;
+  int ctas_per_sm = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  std::string last_error;
+  int64_t launches = 0;
+  bool qp_built = false;
+  bool have_step = false;
+  // host copies of the segment offsets and the generator permutation
+  int* h_bus_off = nullptr;
+  int* h_br_off = nullptr;
+  int* h_gen_off = nullptr;
+  int* h_gen_perm = nullptr;   // internal index -> user index (global)
+  int* h_gen_iperm = nullptr;  // user index -> internal index
+  void* allocs[128];
+  int nallocs = 0;
+  // sweep timing (acopf_profile)
+  bool profiling = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double prof_ms = 0.0;
+  int64_t prof_sweeps = 0, prof_iters = 0;
+  // warm start staged by acopf_set_warm_start
+  bool warm_x = false, warm_lam = false, warm_rho = false;
+};
+
+// kernels, launchers (defined in the .cu files)
+void launch_setup(Ctx& c);
+void launch_flat_start(Ctx& c);
+void launch_build(Ctx& c, bool do_export);
+void launch_admm_reset(Ctx& c, int keep_lambda);
+acopf_status launch_sweep(Ctx& c, const admm_options& o, int fixed_iters);
+void launch_step(Ctx& c);
+void launch_merit(Ctx& c);
+void launch_accept_and_kkt(Ctx& c);
+void launch_fill_rho(Ctx& c, double rho);
+
+inline unsigned nblk(long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace acopf

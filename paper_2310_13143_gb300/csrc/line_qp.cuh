@@ -1,0 +1,288 @@
+// The per-branch line subproblem of eq. line_kernel as a 4-variable QP,
+// solved by the augmented Lagrangian method with a projected Newton inner
+// solver (Sec. IV-A).  Host and device code: the sweep kernel calls it per
+// branch, and the same code compiles on the host for unit checks.
+#pragma once
+
+#include <math.h>
+
+#ifndef ACOPF_HD
+#define ACOPF_HD __host__ __device__
+#endif
+
+namespace acopf {
+
+template <typename T>
+struct Tol;
+template <>
+struct Tol<double> {
+  static constexpr double newton = 1e-13;
+  static constexpr double alm = 1e-11;
+};
+template <>
+struct Tol<float> {
+  static constexpr float newton = 2e-6f;
+  static constexpr float alm = 2e-6f;
+};
+
+// ---------------------------------------------------- small dense helpers
+template <typename T>
+ACOPF_HD inline void symv4(const T q[10], const T x[4], T y[4]) {
+  y[0] = q[0] * x[0] + q[1] * x[1] + q[2] * x[2] + q[3] * x[3];
+  y[1] = q[1] * x[0] + q[4] * x[1] + q[5] * x[2] + q[6] * x[3];
+  y[2] = q[2] * x[0] + q[5] * x[1] + q[7] * x[2] + q[8] * x[3];
+  y[3] = q[3] * x[0] + q[6] * x[1] + q[8] * x[2] + q[9] * x[3];
+}
+
+template <typename T>
+ACOPF_HD inline T clampv(T v, T lo, T hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Solve H p = r for packed symmetric positive definite H (Cholesky). Returns false on breakdown.
+template <typename T>
+ACOPF_HD inline bool chol4_solve(const T h[10], const T r[4], T p[4]) {
+  T a00 = h[0], a01 = h[1], a02 = h[2], a03 = h[3], a11 = h[4], a12 = h[5], a13 = h[6], a22 = h[7], a23 = h[8],
+    a33 = h[9];
+  if (!(a00 > T(0))) return false;
+  T l00 = sqrt(a00);
+  T i00 = T(1) / l00;
+  T l10 = a01 * i00, l20 = a02 * i00, l30 = a03 * i00;
+  T d1 = a11 - l10 * l10;
+  if (!(d1 > T(0))) return false;
+  T l11 = sqrt(d1);
+  T i11 = T(1) / l11;
+  T l21 = (a12 - l20 * l10) * i11, l31 = (a13 - l30 * l10) * i11;
+  T d2 = a22 - l20 * l20 - l21 * l21;
+  if (!(d2 > T(0))) return false;
+  T l22 = sqrt(d2);
+  T i22 = T(1) / l22;
+  T l32 = (a23 - l30 * l20 - l31 * l21) * i22;
+  T d3 = a33 - l30 * l30 - l31 * l31 - l32 * l32;
+  if (!(d3 > T(0))) return false;
+  T l33 = sqrt(d3);
+  T i33 = T(1) / l33;
+  T y0 = r[0] * i00;
+  T y1 = (r[1] - l10 * y0) * i11;
+  T y2 = (r[2] - l20 * y0 - l21 * y1) * i22;
+  T y3 = (r[3] - l30 * y0 - l31 * y1 - l32 * y2) * i33;
+  p[3] = y3 * i33;
+  p[2] = (y2 - l32 * p[3]) * i22;
+  p[1] = (y1 - l21 * p[2] - l31 * p[3]) * i11;
+  p[0] = (y0 - l10 * p[1] - l20 * p[2] - l30 * p[3]) * i00;
+  return true;
+}
+
+// ----------------------------------------------------------- line update
+// min 1/2 x'Qx + c'x  s.t. lo <= x <= hi,  R_r x <= rb_r (r < 4, rows that are on)
+//
+// Augmented Lagrangian (Powell-Hestenes-Rockafellar, penalty beta) on the four
+// rows.  Each subproblem  min_{lo<=x<=hi} 1/2 x'Qx + c'x + sum_r psi_r(x),
+// psi_r = (max(0, u_r + beta h_r)^2 - u_r^2) / (2 beta), is piecewise
+// quadratic; it is solved by a semismooth Newton loop that fixes the pieces
+// at the current point and solves the resulting box-constrained QP exactly by
+// a primal active-set method (the bounds play the role of TRON's projected
+// search; with four variables the active-set method terminates in a few
+// factorisations).
+template <typename T>
+struct LineQP {
+  T q[10], c[4], lo[4], hi[4];
+  T R[4][4], rb[4];
+  bool on[4];
+};
+
+// packed index of (i, j)
+ACOPF_HD inline int pk(int i, int j) {
+  const int t[4][4] = {{0, 1, 2, 3}, {1, 4, 5, 6}, {2, 5, 7, 8}, {3, 6, 8, 9}};
+  return t[i][j];
+}
+
+template <typename T>
+struct Eps;
+template <>
+struct Eps<double> {
+  static constexpr double v = 2.2204460492503131e-16;
+};
+template <>
+struct Eps<float> {
+  static constexpr float v = 1.1920928955078125e-07f;
+};
+
+// Box-constrained strictly convex QP  min 1/2 x'Hx + b'x,  lo <= x <= hi,
+// by the primal active-set method from the feasible start x.  fix[i]: 0 free,
+// -1 at lo, +1 at hi.  Returns the number of factorisations used.
+template <typename T>
+ACOPF_HD inline int box_qp(const T h[10], const T b[4], const T lo[4], const T hi[4], T x[4], int maxit) {
+  int fix[4];
+  bool perm[4];
+  T scale = T(0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    perm[i] = !(lo[i] < hi[i]);
+    if (perm[i]) { x[i] = lo[i]; fix[i] = -1; }
+    else if (x[i] <= lo[i]) { x[i] = lo[i]; fix[i] = -1; }
+    else if (x[i] >= hi[i]) { x[i] = hi[i]; fix[i] = 1; }
+    else fix[i] = 0;
+    scale = fmax(scale, fabs(b[i]));
+  }
+  T hmax = T(0);
+#pragma unroll
+  for (int k = 0; k < 10; ++k) hmax = fmax(hmax, fabs(h[k]));
+  int it = 0;
+  for (; it < maxit; ++it) {
+    // minimiser over the free variables with the others held at their bounds
+    T hh[10], rhs[4], y[4];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) hh[k] = h[k];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (fix[i]) {
+        rhs[i] = T(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) hh[pk(i, j)] = T(0);
+        hh[pk(i, i)] = T(1);
+      } else {
+        T s = -b[i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (fix[j]) s -= h[pk(i, j)] * x[j];
+        rhs[i] = s;
+      }
+    }
+    if (!chol4_solve(hh, rhs, y)) break;
+    if (sizeof(T) < sizeof(double)) {
+      // one step of iterative refinement with the residual formed in FP64:
+      // the line QP's condition number (rho I against rho F'F) reaches 1e4
+      T rr[4], dy[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        double acc = (double)rhs[i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc -= (double)hh[pk(i, j)] * (double)y[j];
+        rr[i] = (T)acc;
+      }
+      if (chol4_solve(hh, rr, dy))
+#pragma unroll
+        for (int i = 0; i < 4; ++i) y[i] += dy[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (fix[i]) y[i] = x[i];
+    // longest feasible step towards y
+    T alpha = T(1);
+    int blk = -1, side = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (fix[i]) continue;
+      T dx = y[i] - x[i];
+      if (y[i] < lo[i] && dx < T(0)) {
+        T a = (lo[i] - x[i]) / dx;
+        if (a < alpha) { alpha = a; blk = i; side = -1; }
+      } else if (y[i] > hi[i] && dx > T(0)) {
+        T a = (hi[i] - x[i]) / dx;
+        if (a < alpha) { alpha = a; blk = i; side = 1; }
+      }
+    }
+    if (blk >= 0) {
+      alpha = alpha < T(0) ? T(0) : alpha;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (!fix[i]) x[i] = clampv(x[i] + alpha * (y[i] - x[i]), lo[i], hi[i]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i == blk) {
+          x[i] = side < 0 ? lo[i] : hi[i];
+          fix[i] = side;
+        }
+      continue;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = y[i];
+    // multipliers of the bounds held: release the one of wrong sign that is largest
+    T g[4];
+    symv4(h, x, g);
+    T xs = T(0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      g[i] += b[i];
+      xs = fmax(xs, fabs(x[i]));
+    }
+    T tol = T(64) * Eps<T>::v * (scale + hmax * xs);
+    int worst = -1;
+    T wv = tol;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (!fix[i] || perm[i]) continue;
+      T v = fix[i] < 0 ? -g[i] : g[i];
+      if (v > wv) { wv = v; worst = i; }
+    }
+    if (worst < 0) return it + 1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (i == worst) fix[i] = 0;
+  }
+  return it;
+}
+
+template <typename T>
+ACOPF_HD inline T row_h(const LineQP<T>& P, int r, const T x[4]) {
+  return P.R[r][0] * x[0] + P.R[r][1] * x[1] + P.R[r][2] * x[2] + P.R[r][3] * x[3] - P.rb[r];
+}
+
+template <typename T>
+ACOPF_HD inline void line_solve(const LineQP<T>& P, T x[4], T u[4], T beta, T alm_tol, int alm_outer, int newton_max,
+                                int* work = nullptr) {
+  for (int outer = 0; outer < alm_outer; ++outer) {
+    if (work) work[1]++;
+    unsigned pat = 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (P.on[r] && u[r] + beta * row_h(P, r, x) > T(0)) pat |= 1u << r;
+    for (int it = 0; it < newton_max; ++it) {
+      // pieces fixed: quadratic beta R R' and linear (u - beta rb) R on the rows in pat
+      T h[10], b[4];
+#pragma unroll
+      for (int k = 0; k < 10; ++k) h[k] = P.q[k];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) b[i] = P.c[i];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (!((pat >> r) & 1u)) continue;
+        const T* Rr = P.R[r];
+        T lin = u[r] - beta * P.rb[r];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          b[i] += lin * Rr[i];
+#pragma unroll
+          for (int j = i; j < 4; ++j) h[pk(i, j)] += beta * Rr[i] * Rr[j];
+        }
+      }
+      int nf = box_qp(h, b, P.lo, P.hi, x, 12);
+      if (work) work[0] += nf;
+      unsigned np = 0;
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (P.on[r] && u[r] + beta * row_h(P, r, x) > T(0)) np |= 1u << r;
+      if (np == pat) break;
+      pat = np;
+    }
+    // multiplier update and feasibility/complementarity test
+    T viol = T(0);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (!P.on[r]) {
+        u[r] = T(0);
+        continue;
+      }
+      T hr = row_h(P, r, x);
+      T un = u[r] + beta * hr;
+      un = un > T(0) ? un : T(0);
+      T m = hr > -un / beta ? hr : -un / beta;
+      viol = fmax(viol, fabs(m));
+      u[r] = un;
+    }
+    if (viol <= alm_tol) break;
+  }
+}
+
+}  // namespace acopf

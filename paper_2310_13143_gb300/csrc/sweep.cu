@@ -1,0 +1,480 @@
+// The ADMM sweep of Algorithm 2 fused into one persistent cooperative kernel.
+//
+// Iteration t:
+//   phase A  one thread per generator (eq. gen_kernel, closed form) and per
+//            branch (eq. line_kernel: 4-variable QP with box, line-limit and
+//            angle rows, solved by an augmented Lagrangian whose subproblems
+//            are solved by projected Newton -- Sec. IV-A);
+//   barrier
+//   phase B  one thread per bus (eq. bus_kernel, closed form from the 2x2
+//            system of the power-balance rows), fused with the multiplier
+//            update of every coupling owned by the bus (eq. multiplier) and
+//            the primal/dual residuals r = x - z, s = rho (z+ - z) (Sec. IV-B),
+//            reduced with warp shuffles and one 64-bit atomicMax per warp;
+//   barrier
+//   every CTA reads the per-instance residual slots and decides, identically,
+//   which instances have converged; finished instances are skipped.
+//
+// The device-wide barrier spins with a clock64 limit: a CTA that waits longer
+// than the limit records an error and the kernel returns (no unbounded wait).
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "line_qp.cuh"
+
+namespace acopf {
+
+template <typename T>
+struct SweepP {
+  Dev d;
+  int max_iter;
+  int fixed;            // 1: run max_iter iterations, no residual test
+  double eps, eps_dual;
+  T beta_scale, alm_tol;
+  int alm_outer, newton_max;
+  long long spin_limit;
+};
+
+// ------------------------------------------------------------- barrier
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// returns false (in every thread of the CTA) when this CTA gave up waiting or
+// another CTA reported that it did
+__device__ bool grid_barrier(unsigned* bar, int* err, long long spin_limit) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    unsigned* count = bar;
+    unsigned* gen = bar + 1;
+    unsigned g0 = ld_acquire(gen);
+    __threadfence();
+    unsigned arrived = atomicAdd(count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      long long t0 = clock64();
+      while (ld_acquire(gen) == g0) {
+        if (clock64() - t0 > spin_limit) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(20);
+      }
+    }
+    __threadfence();
+    // another CTA may have given up: leave together (decided by one thread)
+    if (ok && *(volatile int*)err) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// ------------------------------------------------------------- phases
+template <typename T>
+__device__ __forceinline__ void gen_phase(const SweepP<T>& p, int g) {
+  const Dev& d = p.d;
+  const V4<T>* R = (const V4<T>*)d.grec;
+  V4<T> a = R[g], b = R[d.G + g];
+  V2<T> z = ((const V2<T>*)d.ZG)[g];
+  V2<T> lam = ((const V2<T>*)d.LG)[g];
+  T rho = b.z;
+  // eq. gen_kernel: clamp((rho z - lambda - f') / (f'' + rho)) and clamp((rho z - lambda) / rho)
+  V2<T> x;
+  x.x = clampv((rho * z.x - lam.x - a.x) / (a.y + rho), a.z, a.w);
+  x.y = clampv((rho * z.y - lam.y) / rho, b.x, b.y);
+  ((V2<T>*)d.XG)[g] = x;
+}
+
+template <typename T>
+__device__ __forceinline__ void line_phase(const SweepP<T>& p, int l) {
+  const Dev& d = p.d;
+  const int L = d.L;
+  const V4<T>* R = (const V4<T>*)d.lrec;
+  T rec[56];
+#pragma unroll
+  for (int c = 0; c < kRecChunks; ++c) {
+    V4<T> v = R[c * L + l];
+    rec[4 * c] = v.x;
+    rec[4 * c + 1] = v.y;
+    rec[4 * c + 2] = v.z;
+    rec[4 * c + 3] = v.w;
+  }
+  const V4<T>* Z = (const V4<T>*)d.Z;
+  const V4<T>* LM = (const V4<T>*)d.LAM;
+  V4<T> z0 = Z[2 * l], z1 = Z[2 * l + 1];
+  V4<T> l0 = LM[2 * l], l1 = LM[2 * l + 1];
+  V4<T> uu = ((V4<T>*)d.U)[l];
+  T rho = ((const T*)d.trho_l)[l];
+  // couplings: flows p_ij q_ij p_ji q_ji (F rows 0..3), voltages dbar 0..3
+  T zf[4] = {z0.x, z0.y, z1.x, z1.y}, lf[4] = {l0.x, l0.y, l1.x, l1.y};
+  T zv[4] = {z0.z, z0.w, z1.z, z1.w}, lv[4] = {l0.z, l0.w, l1.z, l1.w};
+  LineQP<T> P;
+#pragma unroll
+  for (int k = 0; k < 10; ++k) P.q[k] = rec[k];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    T s = rec[30 + i] + lv[i] - rho * zv[i];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) s += rec[10 + 4 * f + i] * (lf[f] - rho * zf[f]);
+    P.c[i] = s;
+    P.lo[i] = rec[34 + i];
+    P.hi[i] = rec[38 + i];
+  }
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) P.R[e][i] = rec[42 + 4 * e + i];
+    P.rb[e] = rec[50 + e];
+    P.on[e] = rec[54 + e] > T(0);
+  }
+  T alo = rec[52], ahi = rec[53];
+  bool ang = ahi < T(1e29);
+  P.R[2][0] = T(0); P.R[2][1] = T(1); P.R[2][2] = T(0); P.R[2][3] = T(-1); P.rb[2] = ahi; P.on[2] = ang;
+  P.R[3][0] = T(0); P.R[3][1] = T(-1); P.R[3][2] = T(0); P.R[3][3] = T(1); P.rb[3] = -alo; P.on[3] = ang;
+  T x[4], u[4] = {uu.x, uu.y, uu.z, uu.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x[i] = clampv(zv[i], P.lo[i], P.hi[i]);
+  T qd = fmax(fmax(P.q[0], P.q[4]), fmax(P.q[7], P.q[9]));
+  line_solve(P, x, u, p.beta_scale * qd, p.alm_tol, p.alm_outer, p.newton_max);
+  T xf[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+    xf[f] = rec[10 + 4 * f] * x[0] + rec[10 + 4 * f + 1] * x[1] + rec[10 + 4 * f + 2] * x[2] +
+            rec[10 + 4 * f + 3] * x[3] + rec[26 + f];
+  V4<T>* X = (V4<T>*)d.X;
+  V4<T> o0, o1, ou;
+  o0.x = xf[0]; o0.y = xf[1]; o0.z = x[0]; o0.w = x[1];
+  o1.x = xf[2]; o1.y = xf[3]; o1.z = x[2]; o1.w = x[3];
+  ou.x = u[0]; ou.y = u[1]; ou.z = u[2]; ou.w = u[3];
+  X[2 * l] = o0;
+  X[2 * l + 1] = o1;
+  ((V4<T>*)d.U)[l] = ou;
+}
+
+// Warp-level max of the residuals over runs of lanes that hold the same
+// instance (buses are sorted by instance, so runs are contiguous): a segmented
+// shuffle-down reduction, then one 64-bit atomicMax per run and residual.
+// All 32 lanes must call it; lanes without a bus pass inst = -1.
+__device__ __forceinline__ void res_max2(unsigned long long* slots, int K, int slot, double r, double s, int inst) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    double r2 = __shfl_down_sync(FULL, r, o);
+    double s2 = __shfl_down_sync(FULL, s, o);
+    int k2 = __shfl_down_sync(FULL, inst, o);
+    if (lane + o < 32 && k2 == inst) {
+      r = fmax(r, r2);
+      s = fmax(s, s2);
+    }
+  }
+  int kprev = __shfl_up_sync(FULL, inst, 1);
+  bool leader = (lane == 0 || kprev != inst) && inst >= 0;
+  if (leader) {
+    if (r > 0.0) atomicMax(&slots[(slot * 2 + 0) * K + inst], (unsigned long long)__double_as_longlong(r));
+    if (s > 0.0) atomicMax(&slots[(slot * 2 + 1) * K + inst], (unsigned long long)__double_as_longlong(s));
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void bus_phase(const SweepP<T>& p, int i, bool check, int slot, double& rmax,
+                                          double& smax) {
+  (void)slot;
+  const Dev& d = p.d;
+  V4<T> br = ((const V4<T>*)d.brec)[i];  // pdk qdk gs bs
+  const V4<T>* X = (const V4<T>*)d.X;
+  V4<T>* Z = (V4<T>*)d.Z;
+  V4<T>* LM = (V4<T>*)d.LAM;
+  const V2<T>* XG = (const V2<T>*)d.XG;
+  V2<T>* ZG = (V2<T>*)d.ZG;
+  V2<T>* LG = (V2<T>*)d.LG;
+  const V4<T>* GR = (const V4<T>*)d.grec;
+  const T* rl = (const T*)d.trho_l;
+  int g0 = d.gen_ptr[i], g1 = d.gen_ptr[i + 1];
+  int e0 = d.end_ptr[i], e1 = d.end_ptr[i + 1];
+  // pass 1: the 2x2 system (AQ^-1A') lambda = AQ^-1 c - b, c = lambda + rho x
+  T M11 = 0, M22 = 0, v1 = 0, v2 = 0, Qw = 0, cw = 0, Qt = 0, ct = 0;
+  for (int g = g0; g < g1; ++g) {
+    V2<T> x = XG[g], lm = LG[g];
+    T r = GR[d.G + g].z;
+    M11 += T(1) / r;
+    M22 += T(1) / r;
+    v1 += (lm.x + r * x.x) / r;
+    v2 += (lm.y + r * x.y) / r;
+  }
+  for (int e = e0; e < e1; ++e) {
+    int le = d.end_idx[e];
+    V4<T> x = X[le], lm = LM[le];
+    T r = rl[le >> 1];
+    M11 += T(1) / r;
+    M22 += T(1) / r;
+    v1 -= (lm.x + r * x.x) / r;
+    v2 -= (lm.y + r * x.y) / r;
+    Qw += r;
+    cw += lm.z + r * x.z;
+    Qt += r;
+    ct += lm.w + r * x.w;
+  }
+  T gsh = br.z, bsh = br.w;
+  T iQw = Qw > T(0) ? T(1) / Qw : T(0);  // a bus without branch ends has no voltage copies
+  M11 += gsh * gsh * iQw;
+  M22 += bsh * bsh * iQw;
+  T M12 = -gsh * bsh * iQw;
+  v1 += -gsh * cw * iQw - br.x;
+  v2 += bsh * cw * iQw - br.y;
+  T det = M11 * M22 - M12 * M12;
+  T n1 = (M22 * v1 - M12 * v2) / det;
+  T n2 = (M11 * v2 - M12 * v1) / det;
+  T dw = (cw + gsh * n1 - bsh * n2) * iQw;
+  T dth = (d.isref[i] || !(Qt > T(0))) ? T(0) : ct / Qt;
+  // pass 2: bus-side values, multiplier update (eq. multiplier), residuals
+  double rm = 0, sm = 0;
+  for (int g = g0; g < g1; ++g) {
+    V2<T> x = XG[g], lm = LG[g];
+    T r = GR[d.G + g].z;
+    V2<T> zn, ln;
+    zn.x = (lm.x + r * x.x - n1) / r;
+    zn.y = (lm.y + r * x.y - n2) / r;
+    if (check) {
+      V2<T> zo = ZG[g];
+      sm = fmax(sm, (double)fabs(r * (zn.x - zo.x)));
+      sm = fmax(sm, (double)fabs(r * (zn.y - zo.y)));
+    }
+    T rx = x.x - zn.x, ry = x.y - zn.y;
+    rm = fmax(rm, (double)fmax(fabs(rx), fabs(ry)));
+    ln.x = lm.x + r * rx;
+    ln.y = lm.y + r * ry;
+    ZG[g] = zn;
+    LG[g] = ln;
+  }
+  for (int e = e0; e < e1; ++e) {
+    int le = d.end_idx[e];
+    V4<T> x = X[le], lm = LM[le];
+    T r = rl[le >> 1];
+    V4<T> zn, ln;
+    zn.x = (lm.x + r * x.x + n1) / r;
+    zn.y = (lm.y + r * x.y + n2) / r;
+    zn.z = dw;
+    zn.w = dth;
+    if (check) {
+      V4<T> zo = Z[le];
+      T s1 = fmax(fabs(zn.x - zo.x), fabs(zn.y - zo.y));
+      T s2 = fmax(fabs(zn.z - zo.z), fabs(zn.w - zo.w));
+      sm = fmax(sm, (double)(r * fmax(s1, s2)));
+    }
+    T rx = x.x - zn.x, ry = x.y - zn.y, rw = x.z - zn.z, rt = x.w - zn.w;
+    rm = fmax(rm, (double)fmax(fmax(fabs(rx), fabs(ry)), fmax(fabs(rw), fabs(rt))));
+    ln.x = lm.x + r * rx;
+    ln.y = lm.y + r * ry;
+    ln.z = lm.z + r * rw;
+    ln.w = lm.w + r * rt;
+    Z[le] = zn;
+    LM[le] = ln;
+  }
+  V2<T> zb, nu;
+  zb.x = dw; zb.y = dth;
+  nu.x = n1; nu.y = n2;
+  ((V2<T>*)d.ZB)[i] = zb;
+  ((V2<T>*)d.NU)[i] = nu;
+  // a NaN must not pass the residual test
+  if (!(rm == rm)) rm = 1e300;
+  if (!(sm == sm)) sm = 1e300;
+  rmax = rm;
+  smax = sm;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep(SweepP<T> p) {
+  const Dev& d = p.d;
+  extern __shared__ int s_done[];  // per-instance finished flags, K entries
+  const int K = d.K;
+  const int nthreads = gridDim.x * blockDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) s_done[k] = d.admm_done[k];
+  __syncthreads();
+  int it = 0;
+  bool aborted = false;
+  for (it = 0; it < p.max_iter; ++it) {
+    const int slot = it & 1;
+    // phase A: generators then branches
+    for (int u = tid; u < d.G + d.L; u += nthreads) {
+      if (u < d.G) {
+        if (!s_done[d.gen_inst[u]]) gen_phase(p, u);
+      } else {
+        int l = u - d.G;
+        if (!s_done[d.br_inst[l]]) line_phase(p, l);
+      }
+    }
+    // reset the slot used two iterations ago (read by every CTA before the last barrier)
+    if (blockIdx.x == 0)
+      for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        d.res_slots[(slot * 2 + 0) * K + k] = 0ull;
+        d.res_slots[(slot * 2 + 1) * K + k] = 0ull;
+      }
+    if (!grid_barrier(d.bar, d.err, p.spin_limit)) { aborted = true; break; }
+    // phase B: buses; the loop bound is uniform per warp so that all lanes reduce together
+    for (int i0 = tid - (threadIdx.x & 31); i0 < d.B; i0 += nthreads) {
+      int i = i0 + (threadIdx.x & 31);
+      int k = -1;
+      double rm = 0.0, sm = 0.0;
+      if (i < d.B) {
+        k = d.bus_inst[i];
+        if (s_done[k]) k = -1;
+        else bus_phase(p, i, true, slot, rm, sm);
+      }
+      res_max2(d.res_slots, K, slot, rm, sm, k);
+    }
+    if (!grid_barrier(d.bar, d.err, p.spin_limit)) { aborted = true; break; }
+    if (p.fixed) continue;
+    // residual test (Sec. IV-B), evaluated identically by every CTA
+    int all = 1;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      if (s_done[k]) continue;
+      double r = __longlong_as_double((long long)d.res_slots[(slot * 2 + 0) * K + k]);
+      double s = __longlong_as_double((long long)d.res_slots[(slot * 2 + 1) * K + k]);
+      if (r <= p.eps && s <= p.eps_dual) {
+        s_done[k] = 1;
+        if (blockIdx.x == 0) {
+          d.admm_done[k] = 1;
+          d.admm_iters[k] = it + 1;
+          d.admm_rs[k] = r;
+          d.admm_rs[K + k] = s;
+        }
+      } else {
+        all = 0;
+      }
+    }
+    all = __syncthreads_and(all);
+    if (all) { ++it; break; }
+  }
+  // record the residuals of unfinished instances
+  if (blockIdx.x == 0 && !aborted) {
+    int last = (it - 1) & 1;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      if (d.admm_done[k] && !p.fixed) continue;
+      d.admm_iters[k] = it;
+      d.admm_rs[k] = __longlong_as_double((long long)d.res_slots[(last * 2 + 0) * K + k]);
+      d.admm_rs[K + k] = __longlong_as_double((long long)d.res_slots[(last * 2 + 1) * K + k]);
+    }
+  }
+}
+
+// ADMM state reset: d = 0, z = 0 (and lambda = 0 unless kept); instances that
+// are no longer running keep their state
+template <typename T>
+__global__ void k_admm_reset(Dev d, int keep_lambda) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  V4<T> z4 = {T(0), T(0), T(0), T(0)};
+  V2<T> z2 = {T(0), T(0)};
+  if (n < 2 * d.L) {
+    int k = d.br_inst[n >> 1];
+    if (d.ctl[k].result == ACOPF_RUNNING) {
+      ((V4<T>*)d.X)[n] = z4;
+      ((V4<T>*)d.Z)[n] = z4;
+      if (!keep_lambda) ((V4<T>*)d.LAM)[n] = z4;
+      if (!keep_lambda && (n & 1) == 0) ((V4<T>*)d.U)[n >> 1] = z4;
+    }
+  }
+  if (n < d.G) {
+    int k = d.gen_inst[n];
+    if (d.ctl[k].result == ACOPF_RUNNING) {
+      ((V2<T>*)d.XG)[n] = z2;
+      ((V2<T>*)d.ZG)[n] = z2;
+      if (!keep_lambda) ((V2<T>*)d.LG)[n] = z2;
+    }
+  }
+  if (n < d.B) {
+    int k = d.bus_inst[n];
+    if (d.ctl[k].result == ACOPF_RUNNING) {
+      ((V2<T>*)d.ZB)[n] = z2;
+      ((V2<T>*)d.NU)[n] = z2;
+    }
+  }
+  if (n < d.K) {
+    d.admm_done[n] = d.ctl[n].result == ACOPF_RUNNING ? 0 : 1;
+    d.admm_iters[n] = 0;
+  }
+}
+
+template <typename T>
+static acopf_status run_sweep(Ctx& c, const admm_options& o, int fixed_iters) {
+  Dev& d = c.d;
+  SweepP<T> p;
+  p.d = d;
+  p.max_iter = fixed_iters > 0 ? fixed_iters : o.max_iter;
+  p.fixed = fixed_iters > 0;
+  p.eps = o.eps;
+  p.eps_dual = o.eps_dual > 0 ? o.eps_dual : o.eps;
+  p.beta_scale = (T)o.alm_beta;
+  p.alm_tol = (T)fmax(o.alm_tol, (double)Tol<T>::alm);
+  p.alm_outer = o.alm_max_outer;
+  p.newton_max = o.newton_max;
+  p.spin_limit = o.spin_limit;
+  int threads = c.block_threads;
+  size_t smem = sizeof(int) * (size_t)d.K;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<T>, threads, smem);
+  if (per_sm < 1) return ACOPF_ECUDA;
+  if (c.ctas_per_sm > 0 && c.ctas_per_sm < per_sm) per_sm = c.ctas_per_sm;
+  long work = d.G + d.L;
+  if (d.B > work) work = d.B;
+  long need = (work + threads - 1) / threads;
+  long maxb = (long)per_sm * c.num_sms;
+  int blocks = (int)(need < maxb ? need : maxb);
+  if (blocks < 1) blocks = 1;
+  cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), c.stream);
+  cudaMemsetAsync(d.err, 0, sizeof(int), c.stream);
+  cudaMemsetAsync(d.res_slots, 0, sizeof(unsigned long long) * 4 * d.K, c.stream);
+  void* args[] = {&p};
+  if (c.profiling) cudaEventRecord(c.ev0, c.stream);
+  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_sweep<T>, dim3(blocks), dim3(threads), args, smem, c.stream);
+  c.launches++;
+  if (e != cudaSuccess) {
+    c.last_error = std::string("sweep launch: ") + cudaGetErrorString(e);
+    return ACOPF_ECUDA;
+  }
+  if (c.profiling) {
+    cudaEventRecord(c.ev1, c.stream);
+    cudaEventSynchronize(c.ev1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c.ev0, c.ev1);
+    c.prof_ms += ms;
+    c.prof_sweeps += 1;
+    int mx = 0;
+    std::vector<int> it(d.K);
+    cudaMemcpy(it.data(), d.admm_iters, sizeof(int) * d.K, cudaMemcpyDeviceToHost);
+    for (int k = 0; k < d.K; ++k) mx = it[k] > mx ? it[k] : mx;
+    c.prof_iters += mx;
+  }
+  return ACOPF_OK;
+}
+
+acopf_status launch_sweep(Ctx& c, const admm_options& o, int fixed_iters) {
+  return c.precision == ACOPF_MIXED ? run_sweep<float>(c, o, fixed_iters) : run_sweep<double>(c, o, fixed_iters);
+}
+
+void launch_admm_reset(Ctx& c, int keep_lambda) {
+  Dev& d = c.d;
+  long m = 2L * d.L;
+  if (d.G > m) m = d.G;
+  if (d.B > m) m = d.B;
+  if (d.K > m) m = d.K;
+  if (c.precision == ACOPF_MIXED)
+    k_admm_reset<float><<<nblk(m, 256), 256, 0, c.stream>>>(d, keep_lambda);
+  else
+    k_admm_reset<double><<<nblk(m, 256), 256, 0, c.stream>>>(d, keep_lambda);
+  c.launches++;
+}
+
+}  // namespace acopf

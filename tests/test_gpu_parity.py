@@ -1,0 +1,203 @@
+"""CUDA path vs the FP64 CPU oracle, through the C ABI, on the same seeded inputs.
+
+* QP build (Alg. 1 line 6): every field, element by element, FP64.
+* One ADMM iteration (Alg. 2) from the same random state: every coupling.
+  The GPU solves each line subproblem by its augmented Lagrangian to 1e-11;
+  the oracle solves it exactly, so the FP64 tolerance is 1e-7 relative to the
+  state's scale.
+* Converged QP solve: step and recovered multipliers.
+* Full SQP: objective relative error <= 1e-5 and primal/dual infeasibility
+  <= 1e-4 (the acceptance bar), FP64 and mixed precision.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_13143_gb300 import binding, gridgen as gg
+
+pytestmark = pytest.mark.gpu
+
+
+def _with(g, **kw):
+    return g.__class__(**{**g.__dict__, **kw})
+
+
+def _perturbed(m, rng, scale=0.04):
+    x = m.flat_start()
+    v = m.split(x)
+    v["pg"][:] += scale * rng.standard_normal(m.G)
+    v["qg"][:] += scale * rng.standard_normal(m.G)
+    v["w"][:] = 1.0 + scale * rng.standard_normal(m.B)
+    v["th"][:] = scale * rng.standard_normal(m.B)
+    v["th"][np.flatnonzero(m.grid.bus_type == 3)] = 0.0
+    v["wr"][:] = 1.0 + scale * rng.standard_normal(m.L)
+    v["wi"][:] = scale * rng.standard_normal(m.L)
+    return x
+
+
+GRIDS = {
+    "syn30": lambda: gg.grid_30bus(),
+    "two_bus": lambda: gg.two_bus(lossless=False, rate=1.0),
+    "syn30_shunt_tap": lambda: _with(gg.grid_30bus(), gs=np.linspace(0, 0.03, 30), bs=np.linspace(0.05, 0, 30),
+                                     tap=np.linspace(0.95, 1.05, 41), shift=np.linspace(-0.05, 0.05, 41)),
+    "syn30_nolimits": lambda: _with(gg.grid_30bus(), rate=np.zeros(41), angmin=np.full(41, -7.0),
+                                    angmax=np.full(41, 7.0)),
+    "syn118": lambda: gg.geometric_grid(118, seed=7),
+}
+
+
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_build_matches_oracle(name):
+    g = GRIDS[name]()
+    rng = np.random.default_rng(5)
+    m = oracle.Model(g)
+    x = _perturbed(m, rng)
+    pi = 50 * rng.standard_normal(4 * m.L)
+    delta, rho = 0.3, 2e4
+    ref = m.build(x, pi, delta, 1)
+    s = binding.Solver(g)
+    s.set_iterate(0, x, pi)
+    s.build_qp(delta, rho, True)
+    got = s.get_qp(0)
+    for key in ("flow", "H", "aR", "aI", "bR", "bI", "QH", "gH", "F", "f0", "lo", "hi", "G", "grhs",
+                "gd1", "gd2", "glp", "gup", "glq", "guq", "pdk", "qdk"):
+        a, b = np.asarray(got[key]).reshape(-1), np.asarray(ref[key]).reshape(-1)
+        b = np.where(np.abs(b) >= 1e29, np.sign(b) * 1e30, b)
+        scale = max(1.0, np.abs(b[np.abs(b) < 1e29]).max(initial=0.0))
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-12 * scale, err_msg=key)
+    for key in ("alo", "ahi"):
+        a, b = got[key], ref[key]
+        fin = np.abs(b) < 1e29
+        np.testing.assert_allclose(a[fin], b[fin], atol=1e-12)
+        assert np.all(np.abs(a[~fin]) >= 1e29)
+
+
+def _random_state(m, rng, rho):
+    st = m.new_state(rho)
+    st["zl"][...] = 0.02 * rng.standard_normal(st["zl"].shape)
+    st["ll"][...] = 300 * rng.standard_normal(st["ll"].shape)
+    st["zg"][...] = 0.02 * rng.standard_normal(st["zg"].shape)
+    st["lg"][...] = 300 * rng.standard_normal(st["lg"].shape)
+    # bus copies of w and theta are the bus values (one per bus)
+    g = m.grid
+    zb = 0.01 * rng.standard_normal((m.B, 2))
+    zb[np.flatnonzero(g.bus_type == 3), 1] = 0.0
+    st["zl"][:, 4], st["zl"][:, 5] = zb[g.f, 0], zb[g.f, 1]
+    st["zl"][:, 6], st["zl"][:, 7] = zb[g.t, 0], zb[g.t, 1]
+    st["zb"][...] = zb
+    return st
+
+
+def _gpu_state_from(st):
+    return {"x": st["xl"], "z": st["zl"], "lam": st["ll"], "xg": st["xg"], "zg": st["zg"], "lg": st["lg"],
+            "zb": st["zb"], "nu": st["nu"], "ul": st["ul"]}
+
+
+@pytest.mark.parametrize("name", ["syn30", "syn30_shunt_tap", "syn118", "two_bus"])
+@pytest.mark.parametrize("iters", [1, 3])
+def test_admm_iterations_match_oracle(name, iters):
+    g = GRIDS[name]()
+    rng = np.random.default_rng(11)
+    rho = 2e4
+    m = oracle.Model(g)
+    x = _perturbed(m, rng, 0.02)
+    pi = 20 * rng.standard_normal(4 * m.L)
+    qp = m.build(x, pi, 0.2, 1)
+    st = _random_state(m, rng, rho)
+    s = binding.Solver(g)
+    s.set_iterate(0, x, pi)
+    s.build_qp(0.2, rho, True)
+    s.set_admm_state(0, _gpu_state_from(st))
+    st, _ = m.admm(qp, st, rho=rho, eps=0.0, max_iter=iters)
+    s.admm_iterate(iters)
+    got = s.get_admm_state(0)
+    pairs = [("x", "xl"), ("z", "zl"), ("lam", "ll"), ("xg", "xg"), ("zg", "zg"), ("lg", "lg"), ("zb", "zb"),
+             ("nu", "nu")]
+    for gk, ok in pairs:
+        a, b = got[gk], st[ok]
+        scale = max(1.0, np.abs(b).max())
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-7 * scale, err_msg=f"{gk} after {iters} iterations")
+
+
+def test_converged_qp_step_and_multipliers():
+    g = gg.grid_30bus()
+    m = oracle.Model(g)
+    r = m.sqp(oracle.SqpOptions(max_sqp=2))
+    x, pi = r["x"], r["pi"]
+    # eps / rho must stay above the line solver's own tolerance (1e-11)
+    delta, rho, eps = 0.5, 2e4, 1e-6
+    qp = m.build(x, pi, delta, 1)
+    st, info = m.admm(qp, rho=rho, eps=eps, max_iter=50000)
+    d_ref, pi_ref = m.step(qp, st, x)
+    s = binding.Solver(g)
+    s.set_iterate(0, x, pi)
+    s.admm_solve_qp(delta, binding.default_admm(rho=rho, eps=eps, max_iter=50000, warm=0))
+    d, pi_new = s.get_step(0)
+    res = s.get_residuals(0)
+    assert res["r_inf"] <= eps and res["s_inf"] <= eps
+    np.testing.assert_allclose(d, d_ref, atol=1e-6)
+    np.testing.assert_allclose(pi_new, pi_ref, atol=1e-3 * max(1.0, np.abs(pi_ref).max()))
+
+
+def _sqp_compare(g, precision, tol_obj=1e-5, **opt):
+    m = oracle.Model(g)
+    ref = m.sqp(oracle.SqpOptions(**opt))
+    assert ref["status"] == 0
+    s = binding.Solver(g, precision=precision)
+    o = binding.default_sqp(admm={k: v for k, v in opt.items() if k in ("rho", "eps", "max_iter")},
+                            **{k: v for k, v in opt.items() if k in ("tol", "max_sqp", "mu")})
+    s.sqp_solve(o)
+    res = s.get_residuals(0)
+    sol = s.get_solution(0)
+    assert res["result_name"] == "converged", res
+    assert res["primal"] <= 1e-4 and res["dual"] <= 1e-4, res
+    assert abs(sol["obj"] - ref["obj"]) <= tol_obj * abs(ref["obj"]), (sol["obj"], ref["obj"])
+    return ref, res, sol
+
+
+def test_sqp_fp64_30bus_matches_oracle():
+    ref, res, sol = _sqp_compare(gg.grid_30bus(), "fp64")
+    v = oracle.Model(gg.grid_30bus()).split(ref["x"])
+    np.testing.assert_allclose(sol["pg"], v["pg"], atol=1e-3)
+
+
+def test_sqp_mixed_30bus_matches_oracle():
+    _sqp_compare(gg.grid_30bus(), "mixed")
+
+
+def test_sqp_two_bus_closed_form():
+    c2, c1, pd = (0.02, 0.05), (20.0, 22.0), 0.8
+    g = gg.two_bus(lossless=True, c2=c2, c1=c1, pd2=pd)
+    s = binding.Solver(g)
+    s.sqp_solve(binding.default_sqp(tol=1e-7, admm=dict(rho=1e3, eps=1e-8, max_iter=100000)))
+    res, sol = s.get_residuals(0), s.get_solution(0)
+    assert res["result_name"] == "converged"
+    S = 100.0
+    p1 = (2 * c2[1] * S * S * pd + c1[1] * S - c1[0] * S) / (2 * S * S * (c2[0] + c2[1]))
+    np.testing.assert_allclose(sol["pg"], [p1, pd - p1], atol=1e-6)
+
+
+def test_batched_instances_match_single_solves():
+    grids = [gg.grid_30bus(), gg.grid_30bus(4), gg.grid_30bus(5), gg.two_bus(lossless=False, rate=2.0)]
+    s = binding.Solver(grids)
+    s.sqp_solve()
+    for k, g in enumerate(grids):
+        ref = oracle.Model(g).sqp(oracle.SqpOptions())
+        res, sol = s.get_residuals(k), s.get_solution(k)
+        assert res["result_name"] == "converged", (k, res)
+        assert abs(sol["obj"] - ref["obj"]) <= 1e-5 * abs(ref["obj"]), (k, sol["obj"], ref["obj"])
+
+
+def test_barrier_timeout_is_reported_and_handle_stays_usable():
+    g = gg.geometric_grid(2000, seed=2)
+    s = binding.Solver(g)
+    s.build_qp(1.0, 2e4, True)
+    # a one-cycle wait limit makes CTAs give up at the first device-wide barrier
+    with pytest.raises(binding.AcopfError) as ei:
+        s.admm_iterate(5, binding.default_admm(spin_limit=1))
+    assert ei.value.status == 4
+    s.admm_iterate(2)  # the context is still usable
+    st = s.get_admm_state(0)
+    assert np.all(np.isfinite(st["x"]))
