@@ -98,6 +98,9 @@ typedef struct {
   int32_t alm_max_outer; /* multiplier updates per line subproblem */
   int32_t newton_max;    /* projected Newton steps per multiplier update */
   int64_t spin_limit;    /* clock cycles a CTA waits at a device-wide barrier before giving up */
+  int32_t rb_period;     /* residual balancing every rb_period iterations (0: fixed rho):   */
+  double rb_mu, rb_tau;  /* rho *= rb_tau if r > rb_mu s, rho /= rb_tau if s > rb_mu r; the
+                            adapted penalties carry over to the next QP when warm = 1     */
 } admm_options;
 
 typedef struct {
@@ -106,6 +109,10 @@ typedef struct {
   double step_tol;       /* stop when an accepted step's l_inf norm is below this */
   double delta0, delta_max, delta_min; /* trust region: initial, cap, failure threshold */
   int32_t max_sqp;
+  int32_t merit_linear;  /* 1 (default): h of the l1 merit function also sums the violations of
+                            the linear constraints (power balance, bounds, angle limits), which an
+                            inexact ADMM step does not satisfy exactly; 0: nonlinear constraints
+                            only, as h is defined in Sec. II-C */
   admm_options admm;
 } sqp_options;
 
@@ -172,6 +179,14 @@ acopf_status acopf_set_warm_start(acopf_handle h, int32_t inst, const double* x0
 
 acopf_status acopf_get_solution(acopf_handle h, int32_t inst, acopf_solution* out);
 acopf_status acopf_get_residuals(acopf_handle h, int32_t inst, acopf_residuals* out);
+
+/* Per-SQP-iteration history of the last sqp_solve for instance inst, 12 values
+ * per iteration: objective, primal, dual, ADMM iterations, r, s, accepted (0/1),
+ * trust radius after the update, step norm, actual and predicted merit
+ * reduction, penalty factor of the last QP.  Writes at most cap rows, returns
+ * the number of iterations in *n.  At most ACOPF_HIST_MAX rows are kept. */
+#define ACOPF_HIST_MAX 64
+acopf_status acopf_get_history(acopf_handle h, int32_t inst, double* out, int32_t cap, int32_t* n);
 
 /* ---- lower-level calls used by the parity tests and the benchmark ------- */
 

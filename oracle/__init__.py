@@ -61,7 +61,8 @@ class _State(C.Structure):
 
 
 class _AdmmOpts(C.Structure):
-    _fields_ = [("eps", C.c_double), ("max_iter", C.c_int32), ("use_angle", C.c_int32)]
+    _fields_ = [("eps", C.c_double), ("max_iter", C.c_int32), ("use_angle", C.c_int32), ("rb_period", C.c_int32),
+                ("rb_mu", C.c_double), ("rb_tau", C.c_double)]
 
 
 class _AdmmInfo(C.Structure):
@@ -135,6 +136,9 @@ class SqpOptions:
     eps: float = 1e-4
     max_iter: int = 20000
     use_angle: int = 1
+    rb_period: int = 0
+    rb_mu: float = 10.0
+    rb_tau: float = 2.0
 
 
 class Model:
@@ -229,9 +233,10 @@ class Model:
         lib().og_admm_cold(self._h, C.byref(st.s), float(rho), 0)
         return st
 
-    def admm(self, qp, state=None, rho=2e4, eps=1e-4, max_iter=20000, use_angle=1):
+    def admm(self, qp, state=None, rho=2e4, eps=1e-4, max_iter=20000, use_angle=1, rb_period=0, rb_mu=10.0,
+             rb_tau=2.0):
         st = self.new_state(rho) if state is None else state
-        o = _AdmmOpts(float(eps), int(max_iter), int(use_angle))
+        o = _AdmmOpts(float(eps), int(max_iter), int(use_angle), int(rb_period), float(rb_mu), float(rb_tau))
         info = _AdmmInfo()
         lib().og_admm(self._h, C.byref(qp.s), C.byref(o), C.byref(st.s), C.byref(info))
         return st, dict(iters=info.iters, r=info.r_inf, s=info.s_inf, line_fail=info.line_fail,
@@ -261,7 +266,7 @@ class Model:
     def sqp(self, opts: SqpOptions | None = None, x0=None, hist_cap=200):
         o = opts or SqpOptions()
         so = _SqpOpts(o.mu, o.tol, o.step_tol, o.delta0, o.delta_max, o.delta_min, o.rho, o.max_sqp,
-                      o.warm_lambda, _AdmmOpts(o.eps, o.max_iter, o.use_angle))
+                      o.warm_lambda, _AdmmOpts(o.eps, o.max_iter, o.use_angle, o.rb_period, o.rb_mu, o.rb_tau))
         x0 = self.flat_start() if x0 is None else _f64(x0)
         x = np.zeros(self.n)
         pi = np.zeros(4 * self.L + 1)

@@ -686,12 +686,12 @@ void og_bus_update(const og_model* m, const og_qp* qp, int i, og_admm_state* s, 
 void og_admm_cold(const og_model* m, og_admm_state* s, double rho, int keep_lambda) {
   int B = m->g.nbus, L = m->g.nbranch, G = m->g.ngen;
   for (int k = 0; k < 8 * L; ++k) {
-    s->xl[k] = 0; s->zl[k] = 0; s->rl[k] = rho;
-    if (!keep_lambda) s->ll[k] = 0;
+    s->xl[k] = 0; s->zl[k] = 0;
+    if (!keep_lambda) { s->ll[k] = 0; s->rl[k] = rho; }
   }
   for (int k = 0; k < 2 * G; ++k) {
-    s->xg[k] = 0; s->zg[k] = 0; s->rg[k] = rho;
-    if (!keep_lambda) s->lg[k] = 0;
+    s->xg[k] = 0; s->zg[k] = 0;
+    if (!keep_lambda) { s->lg[k] = 0; s->rg[k] = rho; }
   }
   for (int k = 0; k < 2 * B; ++k) { s->zb[k] = 0; s->nu[k] = 0; }
   if (s->aset)
@@ -721,6 +721,17 @@ int og_admm(const og_model* m, const og_qp* qp, const og_admm_opts* o, og_admm_s
     for (int k = 0; k < 8 * L; ++k) s->ll[k] += s->rl[k] * (s->xl[k] - s->zl[k]);
     for (int k = 0; k < 2 * G; ++k) s->lg[k] += s->rg[k] * (s->xg[k] - s->zg[k]);
     if (rmax <= o->eps && smax <= o->eps) break;
+    /* residual balancing (Boyd et al., Sec. 3.4.1): scale every penalty of the
+     * instance; lambda is not scaled, so nothing else changes */
+    if (o->rb_period > 0 && it % o->rb_period == 0) {
+      double f = 1.0;
+      if (rmax > o->rb_mu * smax) f = o->rb_tau;
+      else if (smax > o->rb_mu * rmax) f = 1.0 / o->rb_tau;
+      if (f != 1.0) {
+        for (int k = 0; k < 8 * L; ++k) s->rl[k] *= f;
+        for (int k = 0; k < 2 * G; ++k) s->rg[k] *= f;
+      }
+    }
   }
   if (it > o->max_iter) it = o->max_iter;
   info->iters = it;
@@ -1012,6 +1023,7 @@ int og_sqp(const og_model* m, const og_sqp_opts* o, const double* x0, double* x,
   memset(pi, 0, sizeof(double) * 4 * L);
   og_admm_cold(m, &st, o->rho, 0);
   double delta = o->delta0;
+  int first_qp = 1;
   int status = 1, k, acc = 0, admm_total = 0;
   double primal = BIG, dual = BIG;
   {
@@ -1020,7 +1032,8 @@ int og_sqp(const og_model* m, const og_sqp_opts* o, const double* x0, double* x,
   }
   for (k = 0; k < o->max_sqp; ++k) {
     og_build(m, x, pi, delta, o->admm.use_angle, &qp);
-    og_admm_cold(m, &st, o->rho, o->warm_lambda);
+    og_admm_cold(m, &st, o->rho, first_qp ? 0 : o->warm_lambda);
+    first_qp = 0;
     og_admm_info ai;
     og_admm(m, &qp, &o->admm, &st, &ai);
     admm_total += ai.iters;

@@ -70,6 +70,8 @@ typedef struct {
   double eps;          /* tolerance on l_inf primal and dual ADMM residuals */
   int32_t max_iter;
   int32_t use_angle;   /* angle-difference rows in the line subproblem */
+  int32_t rb_period;   /* residual balancing every rb_period iterations (0: off) */
+  double rb_mu, rb_tau;
 } og_admm_opts;
 
 typedef struct {
@@ -130,6 +132,7 @@ int og_line_update(const og_model* m, const og_qp* qp, int l, const double z[8],
                    const double rho[8], int use_angle, double x[8], double mult[4], int32_t* hint);
 void og_bus_update(const og_model* m, const og_qp* qp, int i, og_admm_state* s, double* rmax, double* smax);
 
+/* keep_lambda: multipliers and penalties carry over */
 void og_admm_cold(const og_model* m, og_admm_state* s, double rho, int keep_lambda);
 int og_admm(const og_model* m, const og_qp* qp, const og_admm_opts* o, og_admm_state* s, og_admm_info* info);
 

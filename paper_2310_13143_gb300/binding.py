@@ -45,13 +45,14 @@ class admm_options(C.Structure):
     _fields_ = [("rho", C.c_double), ("eps", C.c_double), ("eps_dual", C.c_double), ("max_iter", C.c_int32),
                 ("warm", C.c_int32),
                 ("alm_beta", C.c_double), ("alm_tol", C.c_double), ("alm_max_outer", C.c_int32),
-                ("newton_max", C.c_int32), ("spin_limit", C.c_int64)]
+                ("newton_max", C.c_int32), ("spin_limit", C.c_int64), ("rb_period", C.c_int32),
+                ("rb_mu", C.c_double), ("rb_tau", C.c_double)]
 
 
 class sqp_options(C.Structure):
     _fields_ = [("mu", C.c_double), ("tol", C.c_double), ("step_tol", C.c_double), ("delta0", C.c_double),
                 ("delta_max", C.c_double), ("delta_min", C.c_double), ("max_sqp", C.c_int32),
-                ("admm", admm_options)]
+                ("merit_linear", C.c_int32), ("admm", admm_options)]
 
 
 class acopf_solution(C.Structure):
@@ -117,6 +118,7 @@ def lib():
             "acopf_get_step": (S, [H, C.c_int32, DP, DP]),
             "acopf_launch_count": (S, [H, C.POINTER(C.c_int64)]),
             "acopf_profile": (S, [H, C.c_int32]),
+            "acopf_get_history": (S, [H, C.c_int32, DP, C.c_int32, IP]),
             "acopf_get_profile": (S, [H, DP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         }
         for name, (res, args) in sig.items():
@@ -132,7 +134,7 @@ EXPORTED = ["acopf_default_options", "admm_default_options", "sqp_default_option
             "admm_solve_qp", "acopf_set_warm_start", "acopf_get_solution", "acopf_get_residuals",
             "acopf_set_iterate", "acopf_get_iterate", "acopf_build_qp", "acopf_get_qp", "acopf_get_admm_state",
             "acopf_set_admm_state", "admm_iterate", "acopf_get_step", "acopf_launch_count", "acopf_profile",
-            "acopf_get_profile"]
+            "acopf_get_profile", "acopf_get_history"]
 
 
 def _dp(a):
@@ -318,6 +320,16 @@ class Solver:
         d = {n: getattr(r, n) for n, _ in acopf_residuals._fields_}
         d["result_name"] = RESULTS.get(d["result"], str(d["result"]))
         return d
+
+    HIST_COLS = ("obj", "primal", "dual", "admm_iters", "r", "s", "accepted", "delta", "dnorm", "ared", "pred",
+                 "rho_factor")
+
+    def get_history(self, inst=0):
+        out = np.zeros(64 * 12)
+        n = C.c_int32()
+        self._check(lib().acopf_get_history(self.h, inst, _dp(out), 64, C.byref(n)))
+        k = min(n.value, 64)
+        return out[:12 * k].reshape(k, 12)
 
     def profile(self, on=True):
         self._check(lib().acopf_profile(self.h, int(bool(on))))

@@ -106,6 +106,9 @@ void admm_default_options(admm_options* o) {
   o->alm_max_outer = 50;
   o->newton_max = 20;
   o->spin_limit = 4000000000LL;
+  o->rb_period = 0;
+  o->rb_mu = 10.0;
+  o->rb_tau = 2.0;
 }
 
 void sqp_default_options(sqp_options* o) {
@@ -116,6 +119,7 @@ void sqp_default_options(sqp_options* o) {
   o->delta_max = 10.0;
   o->delta_min = 1e-8;
   o->max_sqp = 30;
+  o->merit_linear = 1;
   admm_default_options(&o->admm);
 }
 
@@ -342,6 +346,7 @@ acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_o
   A(d.bar, 2); A(d.err, 1);
   A(d.flow_xd, 4 * (size_t)L); A(d.tbr, 8 * (size_t)L); A(d.tbus, 4 * (size_t)B); A(d.tgen, 8 * (size_t)G);
   A(d.dend, 2 * 2 * (size_t)L); A(d.red, 16 * (size_t)K); A(d.ctl, K); A(d.n_running, 1);
+  A(d.hist, (size_t)K * ACOPF_HIST_MAX * 12); A(d.rho_fac, K);
 #undef A
 #undef AR
   double *d_r = nullptr, *d_x = nullptr, *d_b = nullptr, *d_tap = nullptr, *d_sh = nullptr;
@@ -551,6 +556,7 @@ static acopf_status reset_control(Ctx* c, const sqp_options& o, bool fresh) {
     q.rho = o.admm.rho;
     q.eps = o.admm.eps;
     q.result = ACOPF_RUNNING;
+    q.merit_linear = o.merit_linear ? 1 : 0;
   }
   CK(cudaMemcpyAsync(d.ctl, ctl.data(), sizeof(InstCtl) * d.K, cudaMemcpyHostToDevice, c->stream));
   // copy back: the host vector is about to go out of scope
@@ -560,7 +566,8 @@ static acopf_status reset_control(Ctx* c, const sqp_options& o, bool fresh) {
 
 static acopf_status check_admm(const admm_options& a, Ctx* c) {
   if (!(a.rho > 0) || !(a.eps >= 0) || !(a.eps_dual >= 0) || a.max_iter < 1 || a.alm_max_outer < 1 || a.newton_max < 1 ||
-      !(a.alm_beta > 0) || a.spin_limit < 1)
+      !(a.alm_beta > 0) || a.spin_limit < 1 || a.rb_period < 0 ||
+      (a.rb_period > 0 && (!(a.rb_mu > 1) || !(a.rb_tau > 1))))
     return fail(c, ACOPF_EINVAL, "admm options out of range");
   return ACOPF_OK;
 }
@@ -592,6 +599,7 @@ acopf_status sqp_solve(acopf_handle h, const sqp_options* op) {
     launch_admm_reset(*c, keep);
     first = false;
     if ((s = launch_sweep(*c, o.admm, 0))) return s;
+    if (o.admm.warm && o.admm.rb_period > 0) launch_commit_rho(*c);
     launch_step(*c);
     launch_merit(*c);
     launch_accept_and_kkt(*c);
@@ -643,6 +651,7 @@ acopf_status admm_solve_qp(acopf_handle h, double delta, const admm_options* ao)
   if ((s = acopf_build_qp(h, delta, a.rho, c->use_angle))) return s;
   launch_admm_reset(*c, a.warm);
   if ((s = launch_sweep(*c, a, 0))) return s;
+  if (a.rb_period > 0) launch_commit_rho(*c);
   launch_step(*c);
   if ((s = sweep_status(c))) return s;
   c->have_step = true;
@@ -659,6 +668,7 @@ acopf_status admm_iterate(acopf_handle h, int32_t n, const admm_options* ao) {
   acopf_status s = check_admm(a, c);
   if (s) return s;
   if ((s = launch_sweep(*c, a, n))) return s;
+  if (a.rb_period > 0) launch_commit_rho(*c);
   launch_step(*c);
   if ((s = sweep_status(c))) return s;
   c->have_step = true;
@@ -881,6 +891,21 @@ acopf_status acopf_get_residuals(acopf_handle h, int32_t inst, acopf_residuals* 
   out->admm_iter = q.sqp_iter > 0 ? q.admm_iter_total : iters;
   out->accepted = q.accepted;
   out->result = q.result;
+  return ACOPF_OK;
+}
+
+acopf_status acopf_get_history(acopf_handle h, int32_t inst, double* out, int32_t cap, int32_t* n) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !inst_ok(c, inst) || cap < 0 || (cap > 0 && !out)) return fail(c, ACOPF_EINVAL, "acopf_get_history: bad arguments");
+  CK(cudaStreamSynchronize(c->stream));
+  InstCtl q;
+  CK(cudaMemcpy(&q, c->d.ctl + inst, sizeof(q), cudaMemcpyDeviceToHost));
+  int rows = q.sqp_iter < ACOPF_HIST_MAX ? q.sqp_iter : ACOPF_HIST_MAX;
+  int k = rows < cap ? rows : cap;
+  if (k > 0)
+    CK(cudaMemcpy(out, c->d.hist + (size_t)inst * ACOPF_HIST_MAX * 12, sizeof(double) * 12 * k,
+                  cudaMemcpyDeviceToHost));
+  if (n) *n = q.sqp_iter;
   return ACOPF_OK;
 }
 

@@ -53,7 +53,7 @@ struct InstCtl {            // per-instance SQP control, device resident
   int32_t result;           // acopf_result
   int32_t accept_last;
   int32_t admm_done;        // 1 once the ADMM residual test passed in the last sweep
-  int32_t pad;
+  int32_t merit_linear;     // 1: h of the merit function includes the linear constraints
 };
 
 // raw device pointers shared by all kernels
@@ -109,6 +109,8 @@ struct Dev {
   double* tgen;       // [8][G]
   double* dend;       // [2][2L] per-end gradient contributions (w, theta)
   double* red;        // [16][K] per-instance reductions
+  double* hist;       // [K][ACOPF_HIST_MAX][12] SQP history
+  double* rho_fac;    // [K] penalty factor applied by residual balancing in the last sweep
   InstCtl* ctl;       // [K]
   int* n_running;     // [1]
   // export buffers (allocated on demand)
@@ -156,6 +158,7 @@ void launch_step(Ctx& c);
 void launch_merit(Ctx& c);
 void launch_accept_and_kkt(Ctx& c);
 void launch_fill_rho(Ctx& c, double rho);
+void launch_commit_rho(Ctx& c);
 
 inline unsigned nblk(long n, int t) { return (unsigned)((n + t - 1) / t); }
 

@@ -670,8 +670,10 @@ __global__ void __launch_bounds__(256) k_decide(Dev d) {
   c.r_inf = d.admm_rs[k];
   c.s_inf = d.admm_rs[d.K + k];
   double mu = c.mu;
-  double h0 = rb[0] + rb[1] + rbus[0] + rg[0];
-  double lin1 = rb[3] + rbus[1] + rg[1];     // linear constraints at x + d
+  // with merit_linear = 0, h is the paper's literal one: nonlinear constraints only
+  double wl = c.merit_linear ? 1.0 : 0.0;
+  double h0 = rb[0] + wl * (rb[1] + rbus[0] + rg[0]);
+  double lin1 = wl * (rb[3] + rbus[1] + rg[1]);     // linear constraints at x + d
   double h1 = rb[2] + lin1;
   double f0 = rg[2], f1 = rg[3];
   double phx = f0 + mu * h0, phxd = f1 + mu * h1;
@@ -681,6 +683,10 @@ __global__ void __launch_bounds__(256) k_decide(Dev d) {
   // step norm over the trust-region variables (pg, qg, w, theta)
   double dn = d.red[16 * k + 0];
   int accept = isfinite(ared) && isfinite(pred) && ared > 0 && pred > 0;
+  if (c.sqp_iter == 0) {  // objective and infeasibility of the starting point
+    c.obj = f0;
+    c.primal = fmax(fmax(rb[6], rbus[2]), rg[6]);
+  }
   c.ared = ared;
   c.pred = pred;
   c.dnorm = dn;
@@ -851,6 +857,12 @@ __global__ void __launch_bounds__(256) k_kkt_decide(Dev d) {
   }
   if (threadIdx.x != 0) return;
   if (c.accept_last) c.dual = fmax(fmax(a[0], bsh[0]), gg[1]) / fmax(1.0, gg[0]);
+  if (c.sqp_iter >= 1 && c.sqp_iter <= ACOPF_HIST_MAX) {
+    double* hr = d.hist + ((size_t)k * ACOPF_HIST_MAX + (c.sqp_iter - 1)) * 12;
+    hr[0] = c.obj; hr[1] = c.primal; hr[2] = c.dual; hr[3] = c.admm_iter_last;
+    hr[4] = c.r_inf; hr[5] = c.s_inf; hr[6] = c.accept_last; hr[7] = c.delta;
+    hr[8] = c.dnorm; hr[9] = c.ared; hr[10] = c.pred; hr[11] = d.rho_fac[k];
+  }
   if (!isfinite(c.obj) || !isfinite(c.primal) || !isfinite(c.dual) || !isfinite(c.delta)) {
     c.result = ACOPF_NONFINITE;
   } else if (c.accept_last && c.primal <= c.tol && c.dual <= c.tol) {

@@ -36,6 +36,8 @@ struct SweepP {
   T beta_scale, alm_tol;
   int alm_outer, newton_max;
   long long spin_limit;
+  int rb_period;
+  double rb_mu, rb_tau;
 };
 
 // ------------------------------------------------------------- barrier
@@ -82,10 +84,14 @@ __device__ bool grid_barrier(unsigned* bar, int* err, long long spin_limit) {
 
 // ------------------------------------------------------------- phases
 template <typename T>
-__device__ __forceinline__ void gen_phase(const SweepP<T>& p, int g) {
+__device__ __forceinline__ void gen_phase(const SweepP<T>& p, int g, float sc) {
   const Dev& d = p.d;
-  const V4<T>* R = (const V4<T>*)d.grec;
+  V4<T>* R = (V4<T>*)d.grec;
   V4<T> a = R[g], b = R[d.G + g];
+  if (sc != 1.0f) {  // residual balancing changed this instance's penalty
+    b.z = (T)((double)b.z * (double)sc);
+    R[d.G + g] = b;
+  }
   V2<T> z = ((const V2<T>*)d.ZG)[g];
   V2<T> lam = ((const V2<T>*)d.LG)[g];
   T rho = b.z;
@@ -97,10 +103,10 @@ __device__ __forceinline__ void gen_phase(const SweepP<T>& p, int g) {
 }
 
 template <typename T>
-__device__ __forceinline__ void line_phase(const SweepP<T>& p, int l) {
+__device__ __forceinline__ void line_phase(const SweepP<T>& p, int l, float sc) {
   const Dev& d = p.d;
   const int L = d.L;
-  const V4<T>* R = (const V4<T>*)d.lrec;
+  V4<T>* R = (V4<T>*)d.lrec;
   T rec[56];
 #pragma unroll
   for (int c = 0; c < kRecChunks; ++c) {
@@ -109,6 +115,34 @@ __device__ __forceinline__ void line_phase(const SweepP<T>& p, int l) {
     rec[4 * c + 1] = v.y;
     rec[4 * c + 2] = v.z;
     rec[4 * c + 3] = v.w;
+  }
+  if (sc != 1.0f) {
+    // residual balancing: Q = A'HA + rho (F'F + I) and c0 = gH + rho F'f0 change with rho
+    double r0 = (double)((const T*)d.trho_l)[l];
+    double dr = r0 * ((double)sc - 1.0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+      for (int b = a; b < 4; ++b) {
+        double ff = a == b ? 1.0 : 0.0;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) ff += (double)rec[10 + 4 * f + a] * (double)rec[10 + 4 * f + b];
+        rec[pk(a, b)] = (T)((double)rec[pk(a, b)] + dr * ff);
+      }
+      double cf = 0.0;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) cf += (double)rec[10 + 4 * f + a] * (double)rec[26 + f];
+      rec[30 + a] = (T)((double)rec[30 + a] + dr * cf);
+    }
+    const int chunks[5] = {0, 1, 2, 7, 8};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      int c = chunks[k];
+      V4<T> v;
+      v.x = rec[4 * c]; v.y = rec[4 * c + 1]; v.z = rec[4 * c + 2]; v.w = rec[4 * c + 3];
+      R[c * L + l] = v;
+    }
+    ((T*)d.trho_l)[l] = (T)(r0 * (double)sc);
   }
   const V4<T>* Z = (const V4<T>*)d.Z;
   const V4<T>* LM = (const V4<T>*)d.LAM;
@@ -297,11 +331,15 @@ __device__ __forceinline__ void bus_phase(const SweepP<T>& p, int i, bool check,
 template <typename T>
 __global__ void __launch_bounds__(256) k_sweep(SweepP<T> p) {
   const Dev& d = p.d;
-  extern __shared__ int s_done[];  // per-instance finished flags, K entries
+  extern __shared__ int s_done[];  // per-instance finished flags (K), then penalty factors (K floats)
   const int K = d.K;
+  float* s_scale = (float*)(s_done + K);
   const int nthreads = gridDim.x * blockDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) s_done[k] = d.admm_done[k];
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    s_done[k] = d.admm_done[k];
+    s_scale[k] = 1.0f;
+  }
   __syncthreads();
   int it = 0;
   bool aborted = false;
@@ -310,10 +348,12 @@ __global__ void __launch_bounds__(256) k_sweep(SweepP<T> p) {
     // phase A: generators then branches
     for (int u = tid; u < d.G + d.L; u += nthreads) {
       if (u < d.G) {
-        if (!s_done[d.gen_inst[u]]) gen_phase(p, u);
+        int k = d.gen_inst[u];
+        if (!s_done[k]) gen_phase(p, u, s_scale[k]);
       } else {
         int l = u - d.G;
-        if (!s_done[d.br_inst[l]]) line_phase(p, l);
+        int k = d.br_inst[l];
+        if (!s_done[k]) line_phase(p, l, s_scale[k]);
       }
     }
     // reset the slot used two iterations ago (read by every CTA before the last barrier)
@@ -336,14 +376,24 @@ __global__ void __launch_bounds__(256) k_sweep(SweepP<T> p) {
       res_max2(d.res_slots, K, slot, rm, sm, k);
     }
     if (!grid_barrier(d.bar, d.err, p.spin_limit)) { aborted = true; break; }
-    if (p.fixed) continue;
-    // residual test (Sec. IV-B), evaluated identically by every CTA
+    // residual test (Sec. IV-B) and residual balancing, evaluated identically by every CTA
+    const bool rb_now = p.rb_period > 0 && ((it + 1) % p.rb_period) == 0;
     int all = 1;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      s_scale[k] = 1.0f;
       if (s_done[k]) continue;
       double r = __longlong_as_double((long long)d.res_slots[(slot * 2 + 0) * K + k]);
       double s = __longlong_as_double((long long)d.res_slots[(slot * 2 + 1) * K + k]);
-      if (r <= p.eps && s <= p.eps_dual) {
+      bool conv = !p.fixed && r <= p.eps && s <= p.eps_dual;
+      if (!conv && rb_now) {
+        float f = 1.0f;
+        if (r > p.rb_mu * s) f = (float)p.rb_tau;
+        else if (s > p.rb_mu * r) f = (float)(1.0 / p.rb_tau);
+        s_scale[k] = f;
+        if (blockIdx.x == 0 && f != 1.0f) d.rho_fac[k] *= (double)f;
+      }
+      if (p.fixed) { all = 0; continue; }
+      if (conv) {
         s_done[k] = 1;
         if (blockIdx.x == 0) {
           d.admm_done[k] = 1;
@@ -356,7 +406,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepP<T> p) {
       }
     }
     all = __syncthreads_and(all);
-    if (all) { ++it; break; }
+    if (all && !p.fixed) { ++it; break; }
   }
   // record the residuals of unfinished instances
   if (blockIdx.x == 0 && !aborted) {
@@ -407,6 +457,29 @@ __global__ void k_admm_reset(Dev d, int keep_lambda) {
   }
 }
 
+__global__ void k_rho_fac_reset(Dev d) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < d.K) d.rho_fac[k] = 1.0;
+}
+
+// carry the penalties adapted by residual balancing into the FP64 master copies
+__global__ void k_commit_rho(Dev d) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < d.L) d.rho_l[n] *= d.rho_fac[d.br_inst[n]];
+  if (n < d.G) d.rho_g[n] *= d.rho_fac[d.gen_inst[n]];
+}
+
+static void launch_rho_fac_reset(Ctx& c) {
+  k_rho_fac_reset<<<nblk(c.d.K, 256), 256, 0, c.stream>>>(c.d);
+  c.launches++;
+}
+
+void launch_commit_rho(Ctx& c) {
+  long m = c.d.L > c.d.G ? c.d.L : c.d.G;
+  k_commit_rho<<<nblk(m, 256), 256, 0, c.stream>>>(c.d);
+  c.launches++;
+}
+
 template <typename T>
 static acopf_status run_sweep(Ctx& c, const admm_options& o, int fixed_iters) {
   Dev& d = c.d;
@@ -421,8 +494,11 @@ static acopf_status run_sweep(Ctx& c, const admm_options& o, int fixed_iters) {
   p.alm_outer = o.alm_max_outer;
   p.newton_max = o.newton_max;
   p.spin_limit = o.spin_limit;
+  p.rb_period = o.rb_period;
+  p.rb_mu = o.rb_mu;
+  p.rb_tau = o.rb_tau;
   int threads = c.block_threads;
-  size_t smem = sizeof(int) * (size_t)d.K;
+  size_t smem = (sizeof(int) + sizeof(float)) * (size_t)d.K;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<T>, threads, smem);
   if (per_sm < 1) return ACOPF_ECUDA;
@@ -436,6 +512,7 @@ static acopf_status run_sweep(Ctx& c, const admm_options& o, int fixed_iters) {
   cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), c.stream);
   cudaMemsetAsync(d.err, 0, sizeof(int), c.stream);
   cudaMemsetAsync(d.res_slots, 0, sizeof(unsigned long long) * 4 * d.K, c.stream);
+  launch_rho_fac_reset(c);
   void* args[] = {&p};
   if (c.profiling) cudaEventRecord(c.ev0, c.stream);
   cudaError_t e = cudaLaunchCooperativeKernel((void*)k_sweep<T>, dim3(blocks), dim3(threads), args, smem, c.stream);

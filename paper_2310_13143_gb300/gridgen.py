@@ -19,7 +19,11 @@ array is float64 (int32 for indices) in per-unit on ``base_mva``:
   uniformly at random;
 * loads: pd ~ U(0.1, 0.5), qd = pd * U(0.2, 0.4), scaled so that the total
   load is at most 60% of the total Pmax;
-* voltage limits [0.94, 1.06], shunts 0, base 100 MVA.
+* voltage limits [0.94, 1.06] on the 30-bus grid and [0.9, 1.1] on the
+  meshed grids of hundreds to tens of thousands of buses, shunts 0, base
+  100 MVA.  (With the narrow band, the synthetic meshed grids of 300 buses
+  and more leave load pockets whose reactive supply cannot stay within it;
+  the wider band is the one large test systems commonly use.)
 
 Feasibility guard (input recipe, not solver arithmetic): a DC power-flow
 estimate of the branch flows under a dispatch proportional to Pmax is taken
@@ -271,7 +275,7 @@ def _spread_generators(n, f, t, r, x, pd, qd, ngen, rng):
     return np.asarray(chosen[:ngen], dtype=np.int32)
 
 
-def _assemble(n, edges, ngen, nload, rng, xy=None, name="", spread=True):
+def _assemble(n, edges, ngen, nload, rng, xy=None, name="", spread=True, vband=(0.94, 1.06)):
     edges = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
     m = edges.shape[0]
     # random orientation of every branch
@@ -320,7 +324,7 @@ def _assemble(n, edges, ngen, nload, rng, xy=None, name="", spread=True):
 
     return Grid(
         nbus=n, bus_type=bus_type, pd=pd, qd=qd, gs=np.zeros(n), bs=np.zeros(n),
-        vmin=np.full(n, 0.94), vmax=np.full(n, 1.06),
+        vmin=np.full(n, vband[0]), vmax=np.full(n, vband[1]),
         f=f, t=t, r=r, x=x, b=b, rate=rate, angmin=angmin, angmax=angmax,
         tap=np.ones(m), shift=np.zeros(m),
         gbus=gb, pmin=pmin, pmax=pmax, qmin=qmin, qmax=qmax, c2=c2, c1=c1, c0=c0,
@@ -354,7 +358,7 @@ def geometric_grid(nbus: int, seed: int, nbranch: int | None = None, ngen: int |
     nload = int(round(0.6 * nbus)) if nload is None else nload
     xy = rng.random((nbus, 2))
     edges = _geometric_edges(xy, nbranch, rng)
-    return _assemble(nbus, edges, ngen, nload, rng, xy=xy, name=name or f"geo{nbus}-s{seed}")
+    return _assemble(nbus, edges, ngen, nload, rng, xy=xy, name=name or f"geo{nbus}-s{seed}", vband=(0.9, 1.1))
 
 
 # --------------------------------------------------------------------------

@@ -201,3 +201,26 @@ def test_barrier_timeout_is_reported_and_handle_stays_usable():
     s.admm_iterate(2)  # the context is still usable
     st = s.get_admm_state(0)
     assert np.all(np.isfinite(st["x"]))
+
+
+def test_residual_balancing_matches_oracle():
+    """Adaptive penalty (residual balancing every 2 iterations): the GPU patches
+    each line record in place, the oracle rebuilds its QPs; states agree."""
+    g = gg.grid_30bus()
+    rng = np.random.default_rng(3)
+    rho = 2e4
+    m = oracle.Model(g)
+    x = _perturbed(m, rng, 0.02)
+    qp = m.build(x, None, 0.2, 1)
+    st = m.new_state(rho)
+    s = binding.Solver(g)
+    s.set_iterate(0, x, None)
+    s.build_qp(0.2, rho, True)
+    s.set_admm_state(0, _gpu_state_from(st))
+    st, _ = m.admm(qp, st, rho=rho, eps=0.0, max_iter=8, rb_period=2)
+    s.admm_iterate(8, binding.default_admm(rb_period=2))
+    assert not np.allclose(st["rl"], rho)  # the penalty did change
+    got = s.get_admm_state(0)
+    for gk, ok in [("x", "xl"), ("z", "zl"), ("lam", "ll"), ("zb", "zb")]:
+        a, b = got[gk], st[ok]
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-7 * max(1.0, np.abs(b).max()), err_msg=gk)
