@@ -246,6 +246,37 @@ acopf_status acopf_launch_count(acopf_handle h, int64_t* n);
 acopf_status acopf_profile(acopf_handle h, int32_t on);
 acopf_status acopf_get_profile(acopf_handle h, double* sweep_ms, int64_t* sweeps, int64_t* admm_iters);
 
+/* ---- allocation-free sweep (the paper has no counterpart) ----------------
+ *
+ * admm_iterate_static runs exactly the n ADMM iterations admm_iterate runs,
+ * on the QP last built and the current ADMM state of the handle, and then
+ * assembles the step, but allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library call.  It is meant for callers that may not allocate
+ * device memory while they run -- code working inside a pre-sized memory
+ * arena, a real-time loop that cannot afford the implicit device
+ * synchronisation an allocation can cause, or a thread that has no access to
+ * the application's allocator.  (The handle itself is still created, with its
+ * allocations, beforehand by acopf_create.)
+ *
+ * The sweep kernel's scratch -- its device-wide barrier counters, error flag,
+ * per-instance residual slots, finished flags and penalty factors -- lives in
+ * one fixed array in device memory, sized for ACOPF_STATIC_MAX_INSTANCES
+ * instances (about 180 KB).  Every GPU that loads the library holds that
+ * array until the process exits.  The first call on a device looks up the
+ * array's device address, so make that first call before any stream capture.
+ * All calls share the array and each call clears what must start at zero;
+ * calls whose work overlaps on the GPU (two handles on different streams, or
+ * two threads) race on it and must be serialised by the caller.
+ *
+ * n >= 1 iterations, o as for admm_iterate.  rs and iters are caller-owned
+ * DEVICE buffers: rs receives 2*K doubles (r of every instance, then s) of
+ * the last iteration, iters K int32 iteration counts, K = number of instances.
+ * Errors: EINVAL for a NULL buffer, bad options, or a handle with more than
+ * ACOPF_STATIC_MAX_INSTANCES instances; ENOTREADY before any QP was built;
+ * ETIMEOUT as admm_iterate; ECUDA if the device address cannot be obtained. */
+#define ACOPF_STATIC_MAX_INSTANCES 4096
+acopf_status admm_iterate_static(acopf_handle h, int32_t n, const admm_options* o, double* rs, int32_t* iters);
+
 #ifdef __cplusplus
 }
 #endif

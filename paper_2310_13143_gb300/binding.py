@@ -119,6 +119,7 @@ def lib():
             "acopf_launch_count": (S, [H, C.POINTER(C.c_int64)]),
             "acopf_profile": (S, [H, C.c_int32]),
             "acopf_get_history": (S, [H, C.c_int32, DP, C.c_int32, IP]),
+            "admm_iterate_static": (S, [H, C.c_int32, C.POINTER(admm_options), C.c_void_p, C.c_void_p]),
             "acopf_get_profile": (S, [H, DP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         }
         for name, (res, args) in sig.items():
@@ -134,7 +135,7 @@ EXPORTED = ["acopf_default_options", "admm_default_options", "sqp_default_option
             "admm_solve_qp", "acopf_set_warm_start", "acopf_get_solution", "acopf_get_residuals",
             "acopf_set_iterate", "acopf_get_iterate", "acopf_build_qp", "acopf_get_qp", "acopf_get_admm_state",
             "acopf_set_admm_state", "admm_iterate", "acopf_get_step", "acopf_launch_count", "acopf_profile",
-            "acopf_get_profile", "acopf_get_history"]
+            "acopf_get_profile", "acopf_get_history", "admm_iterate_static"]
 
 
 def _dp(a):

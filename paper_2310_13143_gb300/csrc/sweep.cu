@@ -20,6 +20,7 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -554,4 +555,156 @@ void launch_admm_reset(Ctx& c, int keep_lambda) {
   c.launches++;
 }
 
+// ----------------------------------------------------------------------------
+// admm_iterate_static: the sweep of admm_iterate with the kernel's scratch
+// (device-wide barrier counters, error flag, residual slots, per-instance
+// finished flags and penalty factors) taken from a fixed device array instead
+// of memory the handle allocated.  It allocates nothing, for callers that may
+// not allocate device memory while they run (a pre-sized memory arena, a
+// real-time loop that cannot afford cudaMalloc's implicit synchronisation, a
+// thread without access to the application's allocator).
+// ----------------------------------------------------------------------------
+namespace {
+
+constexpr int kStaticMaxInstances = ACOPF_STATIC_MAX_INSTANCES;
+constexpr size_t kStaticHeader = 256;  // barrier count + generation, error flag (padded)
+constexpr size_t kStaticSlots = sizeof(unsigned long long) * 4 * kStaticMaxInstances;
+constexpr size_t kStaticDone = sizeof(int) * kStaticMaxInstances;
+constexpr size_t kStaticFac = sizeof(double) * kStaticMaxInstances;
+constexpr size_t kStaticBytes = kStaticHeader + kStaticSlots + kStaticDone + kStaticFac;
+
+// Shared by every call on a device; it keeps the last call's contents.
+static __device__ __align__(256) unsigned char g_sweep_scratch[kStaticBytes];
+
+// Device address of g_sweep_scratch per device ordinal (host-side copies of the
+// symbol are only stand-ins, not device addresses).
+static void* g_scratch_addr[64] = {};
+
+__global__ void k_static_init(Dev d) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < d.K) {
+    d.admm_done[k] = d.ctl[k].result == ACOPF_RUNNING ? 0 : 1;
+    d.rho_fac[k] = 1.0;
+  }
+}
+
+template <typename T>
+acopf_status run_sweep_static(Ctx& c, const admm_options& o, int n, double* rs, int* iters, unsigned char* base) {
+  Dev d = c.d;
+  d.bar = (unsigned*)base;
+  d.err = (int*)(base + 2 * sizeof(unsigned));
+  d.res_slots = (unsigned long long*)(base + kStaticHeader);
+  d.admm_done = (int*)(base + kStaticHeader + kStaticSlots);
+  d.rho_fac = (double*)(base + kStaticHeader + kStaticSlots + kStaticDone);
+  d.admm_rs = rs;
+  d.admm_iters = iters;
+  SweepP<T> p;
+  p.d = d;
+  p.max_iter = n;
+  p.fixed = 1;
+  p.eps = o.eps;
+  p.eps_dual = o.eps_dual > 0 ? o.eps_dual : o.eps;
+  p.beta_scale = (T)o.alm_beta;
+  p.alm_tol = (T)fmax(o.alm_tol, (double)Tol<T>::alm);
+  p.alm_outer = o.alm_max_outer;
+  p.newton_max = o.newton_max;
+  p.spin_limit = o.spin_limit;
+  p.rb_period = o.rb_period;
+  p.rb_mu = o.rb_mu;
+  p.rb_tau = o.rb_tau;
+  int threads = c.block_threads;
+  size_t smem = (sizeof(int) + sizeof(float)) * (size_t)d.K;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<T>, threads, smem) != cudaSuccess || per_sm < 1)
+    return ACOPF_ECUDA;
+  if (c.ctas_per_sm > 0 && c.ctas_per_sm < per_sm) per_sm = c.ctas_per_sm;
+  long work = d.G + d.L;
+  if (d.B > work) work = d.B;
+  long need = (work + threads - 1) / threads;
+  long maxb = (long)per_sm * c.num_sms;
+  int blocks = (int)(need < maxb ? need : maxb);
+  if (blocks < 1) blocks = 1;
+  // what must start at zero: barrier counters, error flag, residual slots
+  cudaMemsetAsync(base, 0, kStaticHeader + sizeof(unsigned long long) * 4 * d.K, c.stream);
+  k_static_init<<<nblk(d.K, 256), 256, 0, c.stream>>>(d);
+  void* args[] = {&p};
+  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_sweep<T>, dim3(blocks), dim3(threads), args, smem, c.stream);
+  c.launches += 2;
+  if (e != cudaSuccess) {
+    c.last_error = std::string("admm_iterate_static launch: ") + cudaGetErrorString(e);
+    return ACOPF_ECUDA;
+  }
+  if (o.rb_period > 0) {
+    long m = d.L > d.G ? d.L : d.G;
+    k_commit_rho<<<nblk(m, 256), 256, 0, c.stream>>>(d);
+    c.launches++;
+  }
+  return ACOPF_OK;
+}
+
+}  // namespace
+
 }  // namespace acopf
+
+extern "C" acopf_status admm_iterate_static(acopf_handle h, int32_t n, const admm_options* ao, double* rs,
+                                            int32_t* iters) {
+  using namespace acopf;
+  Ctx* c = (Ctx*)h;
+  if (!c || n < 1 || !ao || !rs || !iters) {
+    if (c) c->last_error = "admm_iterate_static: handle, n >= 1, options and the rs/iters buffers are required";
+    return ACOPF_EINVAL;
+  }
+  const admm_options& o = *ao;
+  if (!(o.rho > 0) || !(o.eps >= 0) || !(o.eps_dual >= 0) || o.alm_max_outer < 1 || o.newton_max < 1 ||
+      !(o.alm_beta > 0) || o.spin_limit < 1 || o.rb_period < 0 ||
+      (o.rb_period > 0 && (!(o.rb_mu > 1) || !(o.rb_tau > 1)))) {
+    c->last_error = "admm_iterate_static: admm options out of range";
+    return ACOPF_EINVAL;
+  }
+  if (c->d.K > kStaticMaxInstances) {
+    c->last_error = "admm_iterate_static: the handle has " + std::to_string(c->d.K) +
+                    " instances; the fixed scratch array holds at most " + std::to_string(kStaticMaxInstances);
+    return ACOPF_EINVAL;
+  }
+  if (!c->qp_built) {
+    c->last_error = "admm_iterate_static: no QP has been built";
+    return ACOPF_ENOTREADY;
+  }
+  if (c->device < 0 || c->device >= 64) {
+    c->last_error = "admm_iterate_static: device ordinal out of range";
+    return ACOPF_EINVAL;
+  }
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) {
+    c->last_error = std::string("admm_iterate_static: cudaSetDevice: ") + cudaGetErrorString(e);
+    return ACOPF_ECUDA;
+  }
+  // one-time set-up per device, with that device current
+  if (!g_scratch_addr[c->device]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_sweep_scratch);
+    if (e != cudaSuccess || !ptr) {
+      c->last_error = std::string("admm_iterate_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+      return ACOPF_ECUDA;
+    }
+    g_scratch_addr[c->device] = ptr;
+  }
+  unsigned char* base = (unsigned char*)g_scratch_addr[c->device];
+  acopf_status s = c->precision == ACOPF_MIXED ? run_sweep_static<float>(*c, o, n, rs, iters, base)
+                                               : run_sweep_static<double>(*c, o, n, rs, iters, base);
+  if (s) return s;
+  launch_step(*c);
+  int err = 0;
+  e = cudaMemcpyAsync(&err, base + 2 * sizeof(unsigned), sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    c->last_error = std::string("admm_iterate_static: ") + cudaGetErrorString(e);
+    return ACOPF_ECUDA;
+  }
+  if (err) {
+    c->last_error = "admm_iterate_static: a CTA timed out at a device-wide barrier";
+    return ACOPF_ETIMEOUT;
+  }
+  c->have_step = true;
+  return ACOPF_OK;
+}
