@@ -265,9 +265,60 @@ def run_gpu(args, rank, world, local_rank):
                              "ms_per_step": 1e3 * ps / nst, "admm_iter_per_s": plain["admm_iters"] / ps,
                              "objective": plain["obj"], "objective_rel_diff_vs_mixed": abs(plain["obj"] - m["obj"]) / abs(plain["obj"]),
                              "avg_sweep_launch_ms": plain["prof"]["sweep_ms"] / max(plain["prof"]["sweeps"], 1)}
+    if world == 1 and not args.no_batched:
+        out["batched_sweep"] = sweep_only(workload_grids("batched"), args.precision, 50, 3, 1)
+        out["batched_sweep"]["workload"] = ("256 correlated load scenarios of the 2,000-bus grid + 64 grids of "
+                                            "118-10,000 buses (log-uniform), one persistent launch, ADMM sweep only")
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(grid, iters_all / max(args.steps, 1), args.cpu_seconds)
     return out
+
+
+def workload_grids(name):
+    from paper_2310_13143_gb300 import gridgen
+
+    if name == "syn2000":
+        return [gridgen.grid_2000bus()]
+    if name == "batched":  # 256 correlated load scenarios of the 2,000-bus grid + 64 uneven grids
+        return gridgen.batched_uneven()
+    if name == "syn70k":
+        return [gridgen.grid_70k()]
+    if name == "syn70k_x16":
+        return gridgen.scenarios_rff(gridgen.grid_70k(), 16, seed=1005)
+    raise ValueError(name)
+
+
+def sweep_only(grids, precision, iters, launches, warmup):
+    """ADMM sweep alone (fixed iteration count) on the QP at the flat start:
+    ADMM iterations/s and the sweep's HBM roofline on a given workload."""
+    import torch
+
+    from paper_2310_13143_gb300 import binding
+
+    s = binding.Solver(grids, precision=precision)
+    stream = torch.cuda.Stream()
+    s.set_stream(stream.cuda_stream)
+    s.build_qp(1.0, 2e4, True)
+    opts = binding.default_admm()
+    for _ in range(warmup):
+        s.admm_iterate(iters, opts)
+    s.profile(True)
+    for _ in range(launches):
+        s.admm_iterate(iters, opts)
+    p = s.get_profile()
+    s.close()
+    B = sum(g.nbus for g in grids)
+    L = sum(g.nbranch for g in grids)
+    G = sum(g.ngen for g in grids)
+    bpi = sweep_bytes_per_iter(B, L, G, 4 if precision == "mixed" else 8)
+    us = 1e3 * p["sweep_ms"] / (iters * launches)
+    hbm, which = _peaks()
+    gbs = bpi / (us * 1e-6) / 1e9
+    return {"instances": len(grids), "buses": B, "branches": L, "generators": G, "precision": precision,
+            "us_per_iter": us, "admm_iter_per_s": 1e6 / us, "instance_iters_per_s": len(grids) * 1e6 / us,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "traffic": None, "peak_source": which, "bytes_per_iter": bpi,
+                         "kernel": "k_sweep<float>" if precision == "mixed" else "k_sweep<double>"}}
 
 
 def cpu_baseline(grid, admm_iters_per_solve, seconds):
@@ -340,6 +391,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--workload", default="syn2000", choices=["syn2000", "batched", "syn70k", "syn70k_x16"])
+    ap.add_argument("--sweep-iters", type=int, default=0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -352,6 +406,19 @@ def main():
         import torch
 
         torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if args.sweep_iters > 0:  # ADMM sweep alone on a workload (profiling and roofline studies)
+        from paper_2310_13143_gb300.build import build
+
+        build()
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        r = sweep_only(workload_grids(args.workload), args.precision, args.sweep_iters, args.steps, args.warmup)
+        r.update({"metric": "ADMM iter/s (sweep only)", "value": r["admm_iter_per_s"], "unit": "iter/s",
+                  "workload": args.workload, "steps": args.steps, "warmup": args.warmup})
+        if rank == 0:
+            print(json.dumps(r), flush=True)
+        return
     out = run_gpu(args, rank, world, local_rank)
     if rank == 0 and out is not None:
         print(json.dumps(out), flush=True)

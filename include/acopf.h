@@ -245,6 +245,17 @@ acopf_status acopf_launch_count(acopf_handle h, int64_t* n);
  * acopf_profile always resets the totals. */
 acopf_status acopf_profile(acopf_handle h, int32_t on);
 acopf_status acopf_get_profile(acopf_handle h, double* sweep_ms, int64_t* sweeps, int64_t* admm_iters);
+/* While profiling, CTA 0 of the sweep reads the global timer at each phase
+ * boundary: ns[0] its own phase A (generators, branches), ns[1] its wait at
+ * the first device-wide barrier, ns[2] its phase B (buses), ns[3] the second
+ * barrier plus the residual test; summed over iterations since acopf_profile. */
+acopf_status acopf_get_profile_phases(acopf_handle h, double* ns);
+
+/* Launch shape of the ADMM sweep (the autotuner's knobs): threads per CTA
+ * (32..256, multiple of 32; 0 keeps), resident CTAs per SM (0 = as many as
+ * fit; -1 keeps), and for the FP32 sweep the number of shared-memory
+ * branch-tile buffers (1 or 2; 0 keeps). */
+acopf_status acopf_tune(acopf_handle h, int32_t block_threads, int32_t ctas_per_sm, int32_t sweep_stages);
 
 /* ---- allocation-free sweep (the paper has no counterpart) ----------------
  *

@@ -120,6 +120,8 @@ def lib():
             "acopf_profile": (S, [H, C.c_int32]),
             "acopf_get_history": (S, [H, C.c_int32, DP, C.c_int32, IP]),
             "admm_iterate_static": (S, [H, C.c_int32, C.POINTER(admm_options), C.c_void_p, C.c_void_p]),
+            "acopf_get_profile_phases": (S, [H, DP]),
+            "acopf_tune": (S, [H, C.c_int32, C.c_int32, C.c_int32]),
             "acopf_get_profile": (S, [H, DP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         }
         for name, (res, args) in sig.items():
@@ -135,7 +137,8 @@ EXPORTED = ["acopf_default_options", "admm_default_options", "sqp_default_option
             "admm_solve_qp", "acopf_set_warm_start", "acopf_get_solution", "acopf_get_residuals",
             "acopf_set_iterate", "acopf_get_iterate", "acopf_build_qp", "acopf_get_qp", "acopf_get_admm_state",
             "acopf_set_admm_state", "admm_iterate", "acopf_get_step", "acopf_launch_count", "acopf_profile",
-            "acopf_get_profile", "acopf_get_history", "admm_iterate_static"]
+            "acopf_get_profile", "acopf_get_history", "admm_iterate_static", "acopf_get_profile_phases",
+            "acopf_tune"]
 
 
 def _dp(a):
@@ -340,6 +343,14 @@ class Solver:
         n, it = C.c_int64(), C.c_int64()
         self._check(lib().acopf_get_profile(self.h, C.byref(ms), C.byref(n), C.byref(it)))
         return dict(sweep_ms=ms.value, sweeps=n.value, admm_iters=it.value)
+
+    def get_profile_phases(self):
+        ns = np.zeros(4)
+        self._check(lib().acopf_get_profile_phases(self.h, _dp(ns)))
+        return dict(phase_a_ns=ns[0], wait1_ns=ns[1], phase_b_ns=ns[2], wait2_ns=ns[3])
+
+    def tune(self, block_threads=0, ctas_per_sm=-1, sweep_stages=0):
+        self._check(lib().acopf_tune(self.h, block_threads, ctas_per_sm, sweep_stages))
 
     def launch_count(self):
         n = C.c_int64()

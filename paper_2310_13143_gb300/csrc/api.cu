@@ -346,7 +346,7 @@ acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_o
   A(d.bar, 2); A(d.err, 1);
   A(d.flow_xd, 4 * (size_t)L); A(d.tbr, 8 * (size_t)L); A(d.tbus, 4 * (size_t)B); A(d.tgen, 8 * (size_t)G);
   A(d.dend, 2 * 2 * (size_t)L); A(d.red, 16 * (size_t)K); A(d.ctl, K); A(d.n_running, 1);
-  A(d.hist, (size_t)K * ACOPF_HIST_MAX * 12); A(d.rho_fac, K);
+  A(d.hist, (size_t)K * ACOPF_HIST_MAX * 12); A(d.rho_fac, K); A(d.phase_ns, 4);
 #undef A
 #undef AR
   double *d_r = nullptr, *d_x = nullptr, *d_b = nullptr, *d_tap = nullptr, *d_sh = nullptr;
@@ -445,6 +445,7 @@ acopf_status acopf_profile(acopf_handle h, int32_t on) {
   c->profiling = on != 0;
   c->prof_ms = 0.0;
   c->prof_sweeps = c->prof_iters = 0;
+  CK(cudaMemsetAsync(c->d.phase_ns, 0, 4 * sizeof(unsigned long long), c->stream));
   return ACOPF_OK;
 }
 
@@ -455,6 +456,31 @@ acopf_status acopf_get_profile(acopf_handle h, double* ms, int64_t* sweeps, int6
   if (ms) *ms = c->prof_ms;
   if (sweeps) *sweeps = c->prof_sweeps;
   if (iters) *iters = c->prof_iters;
+  return ACOPF_OK;
+}
+
+acopf_status acopf_get_profile_phases(acopf_handle h, double* ns) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !ns) return ACOPF_EINVAL;
+  unsigned long long v[4];
+  CK(cudaMemcpyAsync(v, c->d.phase_ns, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < 4; ++k) ns[k] = (double)v[k];
+  return ACOPF_OK;
+}
+
+acopf_status acopf_tune(acopf_handle h, int32_t block_threads, int32_t ctas_per_sm, int32_t sweep_stages) {
+  Ctx* c = (Ctx*)h;
+  if (!c) return ACOPF_EINVAL;
+  if (block_threads > 0) {
+    if (block_threads % 32 || block_threads > 256) return fail(c, ACOPF_EINVAL, "acopf_tune: block_threads must be 32..256, a multiple of 32");
+    c->block_threads = block_threads;
+  }
+  if (ctas_per_sm >= 0) c->ctas_per_sm = ctas_per_sm;
+  if (sweep_stages > 0) {
+    if (sweep_stages > 2) return fail(c, ACOPF_EINVAL, "acopf_tune: sweep_stages must be 1 or 2");
+    c->sweep_stages = sweep_stages;
+  }
   return ACOPF_OK;
 }
 

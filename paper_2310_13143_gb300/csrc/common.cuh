@@ -111,6 +111,7 @@ struct Dev {
   double* red;        // [16][K] per-instance reductions
   double* hist;       // [K][ACOPF_HIST_MAX][12] SQP history
   double* rho_fac;    // [K] penalty factor applied by residual balancing in the last sweep
+  unsigned long long* phase_ns;  // [4] (profiling) CTA 0's time in phase A, first wait, phase B, second wait + test
   InstCtl* ctl;       // [K]
   int* n_running;     // [1]
   // export buffers (allocated on demand)
@@ -144,6 +145,7 @@ struct Ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double prof_ms = 0.0;
   int64_t prof_sweeps = 0, prof_iters = 0;
+  int sweep_stages = 2;  // FP32 sweep: branch-tile buffers per CTA (1 or 2)
   // warm start staged by acopf_set_warm_start
   bool warm_x = false, warm_lam = false, warm_rho = false;
 };

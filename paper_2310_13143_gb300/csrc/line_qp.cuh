@@ -150,21 +150,6 @@ ACOPF_HD inline int box_qp(const T h[10], const T b[4], const T lo[4], const T h
       }
     }
     if (!chol4_solve(hh, rhs, y)) break;
-    if (sizeof(T) < sizeof(double)) {
-      // one step of iterative refinement with the residual formed in FP64:
-      // the line QP's condition number (rho I against rho F'F) reaches 1e4
-      T rr[4], dy[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        double acc = (double)rhs[i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc -= (double)hh[pk(i, j)] * (double)y[j];
-        rr[i] = (T)acc;
-      }
-      if (chol4_solve(hh, rr, dy))
-#pragma unroll
-        for (int i = 0; i < 4; ++i) y[i] += dy[i];
-    }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
       if (fix[i]) y[i] = x[i];
@@ -216,7 +201,25 @@ ACOPF_HD inline int box_qp(const T h[10], const T b[4], const T lo[4], const T h
       T v = fix[i] < 0 ? -g[i] : g[i];
       if (v > wv) { wv = v; worst = i; }
     }
-    if (worst < 0) return it + 1;
+    if (worst < 0) {
+      if (sizeof(T) < sizeof(double)) {
+        // final active set: one step of iterative refinement with the residual
+        // formed in FP64 (the condition number, rho I against rho F'F, reaches 1e4)
+        T rr[4], dy[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          double acc = (double)rhs[i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc -= (double)hh[pk(i, j)] * (double)(fix[j] ? T(0) : x[j]);
+          rr[i] = fix[i] ? T(0) : (T)acc;
+        }
+        if (chol4_solve(hh, rr, dy))
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (!fix[i]) x[i] = clampv(x[i] + dy[i], lo[i], hi[i]);
+      }
+      return it + 1;
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
       if (i == worst) fix[i] = 0;

@@ -19,6 +19,7 @@
 // than the limit records an error and the kernel returns (no unbounded wait).
 #include <cooperative_groups.h>
 #include <math.h>
+#include <stdint.h>
 
 #include <string>
 #include <vector>
@@ -39,7 +40,15 @@ struct SweepP {
   long long spin_limit;
   int rb_period;
   double rb_mu, rb_tau;
+  int stages;     // FP32 sweep: 1 or 2 branch-tile buffers
+  int profile;    // accumulate CTA 0's phase times into d.phase_ns
 };
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // ------------------------------------------------------------- barrier
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -72,7 +81,6 @@ __device__ bool grid_barrier(unsigned* bar, int* err, long long spin_limit) {
           ok = 0;
           break;
         }
-        __nanosleep(20);
       }
     }
     __threadfence();
@@ -81,6 +89,60 @@ __device__ bool grid_barrier(unsigned* bar, int* err, long long spin_limit) {
   }
   __syncthreads();
   return ok != 0;
+}
+
+// ------------------------------------------------ bulk async tile staging
+// Branch tiles are streamed into shared memory by one thread with 1-D bulk
+// copies (cp.async.bulk, completion counted on an mbarrier in bytes) while
+// the CTA solves the previous tile: memory latency overlaps computation
+// without needing high occupancy.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait for the phase with the given parity; false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity, long long limit) {
+  long long t0 = clock64();
+  while (!mbar_test(b, parity))
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(b))
+               : "memory");
+}
+
+constexpr int kTileV4 = 19;  // per branch: 14 record chunks, 2 z, 2 lambda, 1 u (4-vectors)
+
+// copies of branch tile [l0, l0 + n) into a stage of kTileV4 * tile 4-vectors
+template <typename T>
+__device__ __forceinline__ void tile_issue(const Dev& d, int l0, int n, V4<T>* st, int tile, unsigned long long* b) {
+  const unsigned one = (unsigned)(n * sizeof(V4<T>));
+  mbar_arrive_tx(b, 14u * one + 2u * one + 2u * one + one);
+  const V4<T>* R = (const V4<T>*)d.lrec;
+  for (int c = 0; c < kRecChunks; ++c) bulk_g2s(st + c * tile, R + (size_t)c * d.L + l0, one, b);
+  bulk_g2s(st + 14 * tile, (const V4<T>*)d.Z + 2 * (size_t)l0, 2u * one, b);
+  bulk_g2s(st + 16 * tile, (const V4<T>*)d.LAM + 2 * (size_t)l0, 2u * one, b);
+  bulk_g2s(st + 18 * tile, (const V4<T>*)d.U + l0, one, b);
 }
 
 // ------------------------------------------------------------- phases
@@ -103,15 +165,18 @@ __device__ __forceinline__ void gen_phase(const SweepP<T>& p, int g, float sc) {
   ((V2<T>*)d.XG)[g] = x;
 }
 
+// One branch's line subproblem.  rsrc points at chunk 0 of the branch's record;
+// chunk c is at rsrc[c * rstride] (global memory: stride L; a shared-memory tile:
+// stride TILE).  z, lambda, u and rho are passed in.
 template <typename T>
-__device__ __forceinline__ void line_phase(const SweepP<T>& p, int l, float sc) {
+__device__ __forceinline__ void line_compute(const SweepP<T>& p, int l, float sc, const V4<T>* rsrc, int rstride,
+                                             V4<T> z0, V4<T> z1, V4<T> l0, V4<T> l1, V4<T> uu, T rho) {
   const Dev& d = p.d;
   const int L = d.L;
-  V4<T>* R = (V4<T>*)d.lrec;
   T rec[56];
 #pragma unroll
   for (int c = 0; c < kRecChunks; ++c) {
-    V4<T> v = R[c * L + l];
+    V4<T> v = rsrc[c * rstride];
     rec[4 * c] = v.x;
     rec[4 * c + 1] = v.y;
     rec[4 * c + 2] = v.z;
@@ -119,7 +184,8 @@ __device__ __forceinline__ void line_phase(const SweepP<T>& p, int l, float sc) 
   }
   if (sc != 1.0f) {
     // residual balancing: Q = A'HA + rho (F'F + I) and c0 = gH + rho F'f0 change with rho
-    double r0 = (double)((const T*)d.trho_l)[l];
+    V4<T>* R = (V4<T>*)d.lrec;
+    double r0 = (double)rho;
     double dr = r0 * ((double)sc - 1.0);
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -143,14 +209,9 @@ __device__ __forceinline__ void line_phase(const SweepP<T>& p, int l, float sc) 
       v.x = rec[4 * c]; v.y = rec[4 * c + 1]; v.z = rec[4 * c + 2]; v.w = rec[4 * c + 3];
       R[c * L + l] = v;
     }
-    ((T*)d.trho_l)[l] = (T)(r0 * (double)sc);
+    rho = (T)(r0 * (double)sc);
+    ((T*)d.trho_l)[l] = rho;
   }
-  const V4<T>* Z = (const V4<T>*)d.Z;
-  const V4<T>* LM = (const V4<T>*)d.LAM;
-  V4<T> z0 = Z[2 * l], z1 = Z[2 * l + 1];
-  V4<T> l0 = LM[2 * l], l1 = LM[2 * l + 1];
-  V4<T> uu = ((V4<T>*)d.U)[l];
-  T rho = ((const T*)d.trho_l)[l];
   // couplings: flows p_ij q_ij p_ji q_ji (F rows 0..3), voltages dbar 0..3
   T zf[4] = {z0.x, z0.y, z1.x, z1.y}, lf[4] = {l0.x, l0.y, l1.x, l1.y};
   T zv[4] = {z0.z, z0.w, z1.z, z1.w}, lv[4] = {l0.z, l0.w, l1.z, l1.w};
@@ -197,17 +258,28 @@ __device__ __forceinline__ void line_phase(const SweepP<T>& p, int l, float sc) 
   ((V4<T>*)d.U)[l] = ou;
 }
 
+
+template <typename T>
+__device__ __forceinline__ void line_phase(const SweepP<T>& p, int l, float sc) {
+  const Dev& d = p.d;
+  const V4<T>* Z = (const V4<T>*)d.Z;
+  const V4<T>* LM = (const V4<T>*)d.LAM;
+  line_compute(p, l, sc, (const V4<T>*)d.lrec + l, d.L, Z[2 * l], Z[2 * l + 1], LM[2 * l], LM[2 * l + 1],
+               ((const V4<T>*)d.U)[l], ((const T*)d.trho_l)[l]);
+}
+
 // Warp-level max of the residuals over runs of lanes that hold the same
 // instance (buses are sorted by instance, so runs are contiguous): a segmented
-// shuffle-down reduction, then one 64-bit atomicMax per run and residual.
-// All 32 lanes must call it; lanes without a bus pass inst = -1.
-__device__ __forceinline__ void res_max2(unsigned long long* slots, int K, int slot, double r, double s, int inst) {
+// shuffle-down reduction in the sweep precision, then one 64-bit atomicMax per
+// run and residual.  All 32 lanes must call it; lanes without a bus pass inst = -1.
+template <typename T>
+__device__ __forceinline__ void res_max2(unsigned long long* slots, int K, int slot, T r, T s, int inst) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    double r2 = __shfl_down_sync(FULL, r, o);
-    double s2 = __shfl_down_sync(FULL, s, o);
+    T r2 = __shfl_down_sync(FULL, r, o);
+    T s2 = __shfl_down_sync(FULL, s, o);
     int k2 = __shfl_down_sync(FULL, inst, o);
     if (lane + o < 32 && k2 == inst) {
       r = fmax(r, r2);
@@ -217,14 +289,15 @@ __device__ __forceinline__ void res_max2(unsigned long long* slots, int K, int s
   int kprev = __shfl_up_sync(FULL, inst, 1);
   bool leader = (lane == 0 || kprev != inst) && inst >= 0;
   if (leader) {
-    if (r > 0.0) atomicMax(&slots[(slot * 2 + 0) * K + inst], (unsigned long long)__double_as_longlong(r));
-    if (s > 0.0) atomicMax(&slots[(slot * 2 + 1) * K + inst], (unsigned long long)__double_as_longlong(s));
+    double rd = (double)r, sd = (double)s;
+    if (rd > 0.0) atomicMax(&slots[(slot * 2 + 0) * K + inst], (unsigned long long)__double_as_longlong(rd));
+    if (sd > 0.0) atomicMax(&slots[(slot * 2 + 1) * K + inst], (unsigned long long)__double_as_longlong(sd));
   }
 }
 
 template <typename T>
-__device__ __forceinline__ void bus_phase(const SweepP<T>& p, int i, bool check, int slot, double& rmax,
-                                          double& smax) {
+__device__ __forceinline__ void bus_phase(const SweepP<T>& p, int i, bool check, int slot, T& rmax,
+                                          T& smax) {
   (void)slot;
   const Dev& d = p.d;
   V4<T> br = ((const V4<T>*)d.brec)[i];  // pdk qdk gs bs
@@ -238,20 +311,62 @@ __device__ __forceinline__ void bus_phase(const SweepP<T>& p, int i, bool check,
   const T* rl = (const T*)d.trho_l;
   int g0 = d.gen_ptr[i], g1 = d.gen_ptr[i + 1];
   int e0 = d.end_ptr[i], e1 = d.end_ptr[i + 1];
+  // The first ME branch ends and MG generators of the bus are loaded in one
+  // batch and kept in registers for both passes (a bus has 2.7 ends on
+  // average); any further ones are streamed by the remainder loops.
+  constexpr int ME = sizeof(T) == 4 ? 4 : 2, MG = sizeof(T) == 4 ? 2 : 1;
+  const int ne = e1 - e0, ng = g1 - g0;
+  int lid[ME];
+  V4<T> xe[ME], lme[ME], zoe[ME];
+  T re[ME];
+  V2<T> xgc[MG], lgc[MG], zgc[MG];
+  T rgc[MG];
+#pragma unroll
+  for (int k = 0; k < ME; ++k) lid[k] = k < ne ? d.end_idx[e0 + k] : 0;
+#pragma unroll
+  for (int k = 0; k < ME; ++k)
+    if (k < ne) {
+      xe[k] = X[lid[k]];
+      lme[k] = LM[lid[k]];
+      zoe[k] = Z[lid[k]];
+      re[k] = rl[lid[k] >> 1];
+    }
+#pragma unroll
+  for (int k = 0; k < MG; ++k)
+    if (k < ng) {
+      xgc[k] = XG[g0 + k];
+      lgc[k] = LG[g0 + k];
+      zgc[k] = ZG[g0 + k];
+      rgc[k] = GR[d.G + g0 + k].z;
+    }
   // pass 1: the 2x2 system (AQ^-1A') lambda = AQ^-1 c - b, c = lambda + rho x
   T M11 = 0, M22 = 0, v1 = 0, v2 = 0, Qw = 0, cw = 0, Qt = 0, ct = 0;
-  for (int g = g0; g < g1; ++g) {
-    V2<T> x = XG[g], lm = LG[g];
-    T r = GR[d.G + g].z;
+  for (int k = 0; k < ng; ++k) {
+    V2<T> x, lm;
+    T r;
+    if (k < MG) {
+#pragma unroll
+      for (int q = 0; q < MG; ++q)
+        if (q == k) { x = xgc[q]; lm = lgc[q]; r = rgc[q]; }
+    } else {
+      x = XG[g0 + k]; lm = LG[g0 + k]; r = GR[d.G + g0 + k].z;
+    }
     M11 += T(1) / r;
     M22 += T(1) / r;
     v1 += (lm.x + r * x.x) / r;
     v2 += (lm.y + r * x.y) / r;
   }
-  for (int e = e0; e < e1; ++e) {
-    int le = d.end_idx[e];
-    V4<T> x = X[le], lm = LM[le];
-    T r = rl[le >> 1];
+  for (int k = 0; k < ne; ++k) {
+    V4<T> x, lm;
+    T r;
+    if (k < ME) {
+#pragma unroll
+      for (int q = 0; q < ME; ++q)
+        if (q == k) { x = xe[q]; lm = lme[q]; r = re[q]; }
+    } else {
+      int le = d.end_idx[e0 + k];
+      x = X[le]; lm = LM[le]; r = rl[le >> 1];
+    }
     M11 += T(1) / r;
     M22 += T(1) / r;
     v1 -= (lm.x + r * x.x) / r;
@@ -274,42 +389,55 @@ __device__ __forceinline__ void bus_phase(const SweepP<T>& p, int i, bool check,
   T dw = (cw + gsh * n1 - bsh * n2) * iQw;
   T dth = (d.isref[i] || !(Qt > T(0))) ? T(0) : ct / Qt;
   // pass 2: bus-side values, multiplier update (eq. multiplier), residuals
-  double rm = 0, sm = 0;
-  for (int g = g0; g < g1; ++g) {
-    V2<T> x = XG[g], lm = LG[g];
-    T r = GR[d.G + g].z;
+  T rm = T(0), sm = T(0);
+  for (int k = 0; k < ng; ++k) {
+    V2<T> x, lm, zo;
+    T r;
+    if (k < MG) {
+#pragma unroll
+      for (int q = 0; q < MG; ++q)
+        if (q == k) { x = xgc[q]; lm = lgc[q]; zo = zgc[q]; r = rgc[q]; }
+    } else {
+      x = XG[g0 + k]; lm = LG[g0 + k]; zo = ZG[g0 + k]; r = GR[d.G + g0 + k].z;
+    }
     V2<T> zn, ln;
     zn.x = (lm.x + r * x.x - n1) / r;
     zn.y = (lm.y + r * x.y - n2) / r;
     if (check) {
-      V2<T> zo = ZG[g];
-      sm = fmax(sm, (double)fabs(r * (zn.x - zo.x)));
-      sm = fmax(sm, (double)fabs(r * (zn.y - zo.y)));
+      sm = fmax(sm, fabs(r * (zn.x - zo.x)));
+      sm = fmax(sm, fabs(r * (zn.y - zo.y)));
     }
     T rx = x.x - zn.x, ry = x.y - zn.y;
-    rm = fmax(rm, (double)fmax(fabs(rx), fabs(ry)));
+    rm = fmax(rm, fmax(fabs(rx), fabs(ry)));
     ln.x = lm.x + r * rx;
     ln.y = lm.y + r * ry;
-    ZG[g] = zn;
-    LG[g] = ln;
+    ZG[g0 + k] = zn;
+    LG[g0 + k] = ln;
   }
-  for (int e = e0; e < e1; ++e) {
-    int le = d.end_idx[e];
-    V4<T> x = X[le], lm = LM[le];
-    T r = rl[le >> 1];
+  for (int k = 0; k < ne; ++k) {
+    V4<T> x, lm, zo;
+    T r;
+    int le;
+    if (k < ME) {
+#pragma unroll
+      for (int q = 0; q < ME; ++q)
+        if (q == k) { x = xe[q]; lm = lme[q]; zo = zoe[q]; r = re[q]; le = lid[q]; }
+    } else {
+      le = d.end_idx[e0 + k];
+      x = X[le]; lm = LM[le]; zo = Z[le]; r = rl[le >> 1];
+    }
     V4<T> zn, ln;
     zn.x = (lm.x + r * x.x + n1) / r;
     zn.y = (lm.y + r * x.y + n2) / r;
     zn.z = dw;
     zn.w = dth;
     if (check) {
-      V4<T> zo = Z[le];
       T s1 = fmax(fabs(zn.x - zo.x), fabs(zn.y - zo.y));
       T s2 = fmax(fabs(zn.z - zo.z), fabs(zn.w - zo.w));
-      sm = fmax(sm, (double)(r * fmax(s1, s2)));
+      sm = fmax(sm, r * fmax(s1, s2));
     }
     T rx = x.x - zn.x, ry = x.y - zn.y, rw = x.z - zn.z, rt = x.w - zn.w;
-    rm = fmax(rm, (double)fmax(fmax(fabs(rx), fabs(ry)), fmax(fabs(rw), fabs(rt))));
+    rm = fmax(rm, fmax(fmax(fabs(rx), fabs(ry)), fmax(fabs(rw), fabs(rt))));
     ln.x = lm.x + r * rx;
     ln.y = lm.y + r * ry;
     ln.z = lm.z + r * rw;
@@ -323,8 +451,8 @@ __device__ __forceinline__ void bus_phase(const SweepP<T>& p, int i, bool check,
   ((V2<T>*)d.ZB)[i] = zb;
   ((V2<T>*)d.NU)[i] = nu;
   // a NaN must not pass the residual test
-  if (!(rm == rm)) rm = 1e300;
-  if (!(sm == sm)) sm = 1e300;
+  if (!(rm == rm)) rm = T(1e30);
+  if (!(sm == sm)) sm = T(1e30);
   rmax = rm;
   smax = sm;
 }
@@ -332,11 +460,24 @@ __device__ __forceinline__ void bus_phase(const SweepP<T>& p, int i, bool check,
 template <typename T>
 __global__ void __launch_bounds__(256) k_sweep(SweepP<T> p) {
   const Dev& d = p.d;
-  extern __shared__ int s_done[];  // per-instance finished flags (K), then penalty factors (K floats)
+  extern __shared__ __align__(128) int s_done[];  // finished flags (K ints), penalty factors (K floats), tiles
   const int K = d.K;
   float* s_scale = (float*)(s_done + K);
   const int nthreads = gridDim.x * blockDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  // FP32 sweep: branch tiles of blockDim.x are staged in two shared-memory buffers
+  constexpr bool kTiled = sizeof(T) == 4;
+  const int tile = blockDim.x;
+  V4<T>* stage0 = (V4<T>*)(((uintptr_t)(s_scale + K) + 127) & ~(uintptr_t)127);
+  const bool two = p.stages > 1;
+  V4<T>* stage1 = two ? stage0 + kTileV4 * tile : stage0;
+  unsigned long long* tbar = (unsigned long long*)(stage1 + kTileV4 * tile);
+  unsigned tph0 = 0, tph1 = 0;
+  if (kTiled && threadIdx.x == 0) {
+    mbar_init(&tbar[0], 1);
+    mbar_init(&tbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     s_done[k] = d.admm_done[k];
     s_scale[k] = 1.0f;
@@ -344,18 +485,78 @@ __global__ void __launch_bounds__(256) k_sweep(SweepP<T> p) {
   __syncthreads();
   int it = 0;
   bool aborted = false;
+  unsigned long long tp0 = 0, tp1 = 0;
+  const bool prof = p.profile && blockIdx.x == 0 && threadIdx.x == 0;
   for (it = 0; it < p.max_iter; ++it) {
     const int slot = it & 1;
+    if (prof) tp0 = gtimer();
     // phase A: generators then branches
-    for (int u = tid; u < d.G + d.L; u += nthreads) {
-      if (u < d.G) {
-        int k = d.gen_inst[u];
-        if (!s_done[k]) gen_phase(p, u, s_scale[k]);
-      } else {
-        int l = u - d.G;
-        int k = d.br_inst[l];
-        if (!s_done[k]) line_phase(p, l, s_scale[k]);
+    if (!kTiled) {
+      for (int u = tid; u < d.G + d.L; u += nthreads) {
+        if (u < d.G) {
+          int k = d.gen_inst[u];
+          if (!s_done[k]) gen_phase(p, u, s_scale[k]);
+        } else {
+          int l = u - d.G;
+          int k = d.br_inst[l];
+          if (!s_done[k]) line_phase(p, l, s_scale[k]);
+        }
       }
+    } else {
+      for (int g = tid; g < d.G; g += nthreads) {
+        int k = d.gen_inst[g];
+        if (!s_done[k]) gen_phase(p, g, s_scale[k]);
+      }
+      const int ntiles = (d.L + tile - 1) / tile;
+      int t = blockIdx.x;
+      int sidx = 0;
+      if (t < ntiles && threadIdx.x == 0) {
+        asm volatile("fence.proxy.async;" ::: "memory");  // z, lambda were written by generic stores
+        int n0 = d.L - t * tile < tile ? d.L - t * tile : tile;
+        tile_issue(d, t * tile, n0, stage0, tile, &tbar[0]);
+      }
+      bool tile_fail = false;
+      while (t < ntiles) {
+        const int tn = t + gridDim.x;
+        V4<T>* cur = sidx ? stage1 : stage0;
+        if (two && tn < ntiles && threadIdx.x == 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the other stage was read generically
+          int n1 = d.L - tn * tile < tile ? d.L - tn * tile : tile;
+          tile_issue(d, tn * tile, n1, sidx ? stage0 : stage1, tile, &tbar[sidx ^ 1]);
+        }
+        bool ok = mbar_wait(&tbar[sidx], sidx ? tph1 : tph0, p.spin_limit);
+        if (__syncthreads_or(!ok)) {
+          // give the copies in flight a bounded chance to land, then report
+          if (threadIdx.x == 0) {
+            atomicExch(d.err, 1);
+            mbar_wait(&tbar[0], tph0, p.spin_limit);
+            mbar_wait(&tbar[1], tph1, p.spin_limit);
+          }
+          tile_fail = true;
+          break;
+        }
+        if (sidx) tph1 ^= 1u; else tph0 ^= 1u;
+        const int l = t * tile + threadIdx.x;
+        if (l < d.L) {
+          int k = d.br_inst[l];
+          if (!s_done[k]) {
+            const int j = threadIdx.x;
+            line_compute(p, l, s_scale[k], cur + j, tile, cur[14 * tile + 2 * j], cur[14 * tile + 2 * j + 1],
+                         cur[16 * tile + 2 * j], cur[16 * tile + 2 * j + 1], cur[18 * tile + j],
+                         ((const T*)d.trho_l)[l]);
+          }
+        }
+        __syncthreads();  // the stage may be refilled
+        t = tn;
+        if (two) {
+          sidx ^= 1;
+        } else if (t < ntiles && threadIdx.x == 0) {  // one buffer: load the next tile now
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          int n1 = d.L - t * tile < tile ? d.L - t * tile : tile;
+          tile_issue(d, t * tile, n1, stage0, tile, &tbar[0]);
+        }
+      }
+      (void)tile_fail;
     }
     // reset the slot used two iterations ago (read by every CTA before the last barrier)
     if (blockIdx.x == 0)
@@ -363,12 +564,14 @@ __global__ void __launch_bounds__(256) k_sweep(SweepP<T> p) {
         d.res_slots[(slot * 2 + 0) * K + k] = 0ull;
         d.res_slots[(slot * 2 + 1) * K + k] = 0ull;
       }
+    if (prof) { tp1 = gtimer(); atomicAdd(&d.phase_ns[0], tp1 - tp0); }
     if (!grid_barrier(d.bar, d.err, p.spin_limit)) { aborted = true; break; }
+    if (prof) { tp0 = gtimer(); atomicAdd(&d.phase_ns[1], tp0 - tp1); }
     // phase B: buses; the loop bound is uniform per warp so that all lanes reduce together
     for (int i0 = tid - (threadIdx.x & 31); i0 < d.B; i0 += nthreads) {
       int i = i0 + (threadIdx.x & 31);
       int k = -1;
-      double rm = 0.0, sm = 0.0;
+      T rm = T(0), sm = T(0);
       if (i < d.B) {
         k = d.bus_inst[i];
         if (s_done[k]) k = -1;
@@ -376,6 +579,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepP<T> p) {
       }
       res_max2(d.res_slots, K, slot, rm, sm, k);
     }
+    if (prof) { tp1 = gtimer(); atomicAdd(&d.phase_ns[2], tp1 - tp0); }
     if (!grid_barrier(d.bar, d.err, p.spin_limit)) { aborted = true; break; }
     // residual test (Sec. IV-B) and residual balancing, evaluated identically by every CTA
     const bool rb_now = p.rb_period > 0 && ((it + 1) % p.rb_period) == 0;
@@ -407,6 +611,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepP<T> p) {
       }
     }
     all = __syncthreads_and(all);
+    if (prof) atomicAdd(&d.phase_ns[3], gtimer() - tp1);
     if (all && !p.fixed) { ++it; break; }
   }
   // record the residuals of unfinished instances
@@ -481,6 +686,15 @@ void launch_commit_rho(Ctx& c) {
   c.launches++;
 }
 
+// dynamic shared memory of k_sweep<T>: flags and factors of K instances, and
+// for the FP32 sweep two branch-tile stages plus their mbarriers
+template <typename T>
+static size_t sweep_smem(int K, int threads, int stages) {
+  size_t b = (sizeof(int) + sizeof(float)) * (size_t)K;
+  if (sizeof(T) == 4) b = ((b + 127) & ~(size_t)127) + (size_t)stages * kTileV4 * threads * sizeof(V4<T>) + 16 + 128;
+  return b;
+}
+
 template <typename T>
 static acopf_status run_sweep(Ctx& c, const admm_options& o, int fixed_iters) {
   Dev& d = c.d;
@@ -498,11 +712,17 @@ static acopf_status run_sweep(Ctx& c, const admm_options& o, int fixed_iters) {
   p.rb_period = o.rb_period;
   p.rb_mu = o.rb_mu;
   p.rb_tau = o.rb_tau;
+  p.stages = c.sweep_stages;
+  p.profile = c.profiling ? 1 : 0;
   int threads = c.block_threads;
-  size_t smem = (sizeof(int) + sizeof(float)) * (size_t)d.K;
+  size_t smem = sweep_smem<T>(d.K, threads, c.sweep_stages);
+  cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<T>, threads, smem);
-  if (per_sm < 1) return ACOPF_ECUDA;
+  if (per_sm < 1) {
+    c.last_error = "sweep: the kernel does not fit on a multiprocessor";
+    return ACOPF_ECUDA;
+  }
   if (c.ctas_per_sm > 0 && c.ctas_per_sm < per_sm) per_sm = c.ctas_per_sm;
   long work = d.G + d.L;
   if (d.B > work) work = d.B;
@@ -612,8 +832,11 @@ acopf_status run_sweep_static(Ctx& c, const admm_options& o, int n, double* rs, 
   p.rb_period = o.rb_period;
   p.rb_mu = o.rb_mu;
   p.rb_tau = o.rb_tau;
+  p.stages = c.sweep_stages;
+  p.profile = c.profiling ? 1 : 0;
   int threads = c.block_threads;
-  size_t smem = (sizeof(int) + sizeof(float)) * (size_t)d.K;
+  size_t smem = sweep_smem<T>(d.K, threads, c.sweep_stages);
+  cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<T>, threads, smem) != cudaSuccess || per_sm < 1)
     return ACOPF_ECUDA;

@@ -163,20 +163,27 @@ def _geometric_edges(xy: np.ndarray, m: int, rng: np.random.Generator, scale: fl
     for (a, b), d in items:
         if dsu.union(a, b):
             chosen.append((a, b))
-    # join leftover components through their closest pair
-    roots = {dsu.find(i) for i in range(n)}
-    while len(roots) > 1:
-        comp = np.array([dsu.find(i) for i in range(n)])
-        r0 = comp[0]
-        ins = np.flatnonzero(comp == r0)
-        outs = np.flatnonzero(comp != r0)
-        sub = cKDTree(xy[outs])
-        d, j = sub.query(xy[ins], k=1)
-        a = int(ins[int(np.argmin(d))])
-        b = int(outs[int(j[int(np.argmin(d))])])
-        dsu.union(a, b)
-        chosen.append((min(a, b), max(a, b)))
-        roots = {dsu.find(i) for i in range(n)}
+    # join leftover components, each to its nearest point of the others
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+
+    while True:
+        ee = np.array(chosen, dtype=np.int64).reshape(-1, 2)
+        adj = csr_matrix((np.ones(len(ee)), (ee[:, 0], ee[:, 1])), shape=(n, n))
+        ncomp, lab = connected_components(adj, directed=False)
+        if ncomp <= 1:
+            break
+        sizes = np.bincount(lab, minlength=ncomp)
+        for c in np.argsort(sizes, kind="stable")[: ncomp - 1]:
+            ins = np.flatnonzero(lab == c)
+            outs = np.flatnonzero(lab != c)
+            sub = cKDTree(xy[outs])
+            d, j = sub.query(xy[ins], k=1)
+            a = int(ins[int(np.argmin(d))])
+            b = int(outs[int(j[int(np.argmin(d))])])
+            if dsu.union(a, b):
+                chosen.append((min(a, b), max(a, b)))
+            lab[lab == c] = lab[b]
     have = set(chosen)
     tries = 0
     while len(chosen) < m:
@@ -215,7 +222,13 @@ def _dc_flow_estimate(n, f, t, x, pinj, ref):
     keep = np.ones(n, dtype=bool)
     keep[ref] = False
     th = np.zeros(n)
-    th[keep] = spla.spsolve(B[keep][:, keep].tocsc(), pinj[keep])
+    A = B[keep][:, keep]
+    if n <= 20000:
+        th[keep] = spla.spsolve(A.tocsc(), pinj[keep])
+    else:  # direct factorisation fills in badly on large meshed graphs
+        d = A.diagonal()
+        M = spla.LinearOperator(A.shape, matvec=lambda v: v / d)
+        th[keep], _ = spla.cg(A.tocsr(), pinj[keep], rtol=1e-10, maxiter=20000, M=M)
     return bser * (th[f] - th[t])
 
 

@@ -224,3 +224,44 @@ def test_residual_balancing_matches_oracle():
     for gk, ok in [("x", "xl"), ("z", "zl"), ("lam", "ll"), ("zb", "zb")]:
         a, b = got[gk], st[ok]
         np.testing.assert_allclose(a, b, rtol=0, atol=1e-7 * max(1.0, np.abs(b).max()), err_msg=gk)
+
+
+@pytest.mark.parametrize("name", ["syn30", "syn118", "syn30_shunt_tap"])
+@pytest.mark.parametrize("iters", [1, 3])
+def test_admm_iterations_mixed_precision(name, iters):
+    """FP32 sweep (branch tiles staged in shared memory by bulk copies) against
+    the FP64 oracle: FP32 state within 3e-4 of each array's scale."""
+    g = GRIDS[name]()
+    rng = np.random.default_rng(11)
+    rho = 2e4
+    m = oracle.Model(g)
+    x = _perturbed(m, rng, 0.02)
+    pi = 20 * rng.standard_normal(4 * m.L)
+    qp = m.build(x, pi, 0.2, 1)
+    st = _random_state(m, rng, rho)
+    s = binding.Solver(g, precision="mixed")
+    s.set_iterate(0, x, pi)
+    s.build_qp(0.2, rho, True)
+    s.set_admm_state(0, _gpu_state_from(st))
+    st, _ = m.admm(qp, st, rho=rho, eps=0.0, max_iter=iters)
+    s.admm_iterate(iters)
+    got = s.get_admm_state(0)
+    for gk, ok in [("x", "xl"), ("z", "zl"), ("lam", "ll"), ("xg", "xg"), ("zg", "zg"), ("lg", "lg"), ("zb", "zb")]:
+        a, b = got[gk], st[ok]
+        np.testing.assert_allclose(a, b, rtol=0, atol=3e-4 * max(1.0, np.abs(b).max()), err_msg=f"{gk} {iters}")
+
+
+def test_mixed_sweep_many_tiles_matches_fp64():
+    """A grid large enough for many branch tiles per CTA: the FP32 sweep tracks
+    the FP64 sweep over 20 iterations."""
+    g = gg.geometric_grid(20000, seed=9, nbranch=27000, ngen=4000, nload=12000)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        s = binding.Solver(g, precision=prec)
+        s.build_qp(0.5, 2e4, True)
+        s.admm_iterate(20)
+        out[prec] = s.get_admm_state(0)
+        s.close()
+    for key in ("x", "z", "zb"):
+        a, b = out["mixed"][key], out["fp64"][key]
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-3 * max(1.0, np.abs(b).max()), err_msg=key)
