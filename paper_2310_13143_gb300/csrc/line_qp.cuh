@@ -39,11 +39,52 @@ ACOPF_HD inline T clampv(T v, T lo, T hi) {
   return v < lo ? lo : (v > hi ? hi : v);
 }
 
-// Solve H p = r for packed symmetric positive definite H (Cholesky). Returns false on breakdown.
+// ----------------------------------------------------------- line update
+// min 1/2 x'Qx + c'x  s.t. lo <= x <= hi,  R_r x <= rb_r for the two
+// normalised line-limit rows that are on, and  alo <= x1 - x3 <= ahi  (the
+// angle-difference rows, when ang is set).
+//
+// Augmented Lagrangian (Powell-Hestenes-Rockafellar, penalty beta) on the four
+// rows.  Each subproblem  min_{lo<=x<=hi} 1/2 x'Qx + c'x + sum_r psi_r(x),
+// psi_r = (max(0, u_r + beta h_r)^2 - u_r^2) / (2 beta), is piecewise
+// quadratic; it is solved by a semismooth Newton loop that fixes the pieces
+// at the current point and solves the resulting box-constrained QP exactly by
+// a primal active-set method (the bounds play the role of TRON's projected
+// search; with four variables the active-set method terminates in a few
+// factorisations).
 template <typename T>
-ACOPF_HD inline bool chol4_solve(const T h[10], const T r[4], T p[4]) {
-  T a00 = h[0], a01 = h[1], a02 = h[2], a03 = h[3], a11 = h[4], a12 = h[5], a13 = h[6], a22 = h[7], a23 = h[8],
-    a33 = h[9];
+struct LineQP {
+  T q[10], c[4], lo[4], hi[4];
+  T R[2][4], rb[2];
+  T alo, ahi;
+  bool on[2], ang;
+};
+
+// packed index of (i, j)
+ACOPF_HD inline int pk(int i, int j) {
+  const int t[4][4] = {{0, 1, 2, 3}, {1, 4, 5, 6}, {2, 5, 7, 8}, {3, 6, 8, 9}};
+  return t[i][j];
+}
+
+template <typename T>
+struct Eps;
+template <>
+struct Eps<double> {
+  static constexpr double v = 2.2204460492503131e-16;
+};
+template <>
+struct Eps<float> {
+  static constexpr float v = 1.1920928955078125e-07f;
+};
+
+// Solve A p = r, A = h restricted to the free variables (free bit i set) with
+// unit rows and columns for the fixed ones, by Cholesky.  False on breakdown.
+template <typename T>
+ACOPF_HD inline bool chol4_masked(const T h[10], unsigned fr, const T r[4], T p[4]) {
+  const bool f0 = fr & 1u, f1 = (fr >> 1) & 1u, f2 = (fr >> 2) & 1u, f3 = (fr >> 3) & 1u;
+  T a00 = f0 ? h[0] : T(1), a11 = f1 ? h[4] : T(1), a22 = f2 ? h[7] : T(1), a33 = f3 ? h[9] : T(1);
+  T a01 = f0 && f1 ? h[1] : T(0), a02 = f0 && f2 ? h[2] : T(0), a03 = f0 && f3 ? h[3] : T(0);
+  T a12 = f1 && f2 ? h[5] : T(0), a13 = f1 && f3 ? h[6] : T(0), a23 = f2 && f3 ? h[8] : T(0);
   if (!(a00 > T(0))) return false;
   T l00 = sqrt(a00);
   T i00 = T(1) / l00;
@@ -73,56 +114,38 @@ ACOPF_HD inline bool chol4_solve(const T h[10], const T r[4], T p[4]) {
   return true;
 }
 
-// ----------------------------------------------------------- line update
-// min 1/2 x'Qx + c'x  s.t. lo <= x <= hi,  R_r x <= rb_r (r < 4, rows that are on)
-//
-// Augmented Lagrangian (Powell-Hestenes-Rockafellar, penalty beta) on the four
-// rows.  Each subproblem  min_{lo<=x<=hi} 1/2 x'Qx + c'x + sum_r psi_r(x),
-// psi_r = (max(0, u_r + beta h_r)^2 - u_r^2) / (2 beta), is piecewise
-// quadratic; it is solved by a semismooth Newton loop that fixes the pieces
-// at the current point and solves the resulting box-constrained QP exactly by
-// a primal active-set method (the bounds play the role of TRON's projected
-// search; with four variables the active-set method terminates in a few
-// factorisations).
+// r - sum_j a_j x_j in twice the working precision (Ogita, Rump and Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005: Dot2 with
+// TwoProduct by fused multiply-add and Knuth's TwoSum), rounded once.
 template <typename T>
-struct LineQP {
-  T q[10], c[4], lo[4], hi[4];
-  T R[4][4], rb[4];
-  bool on[4];
-};
-
-// packed index of (i, j)
-ACOPF_HD inline int pk(int i, int j) {
-  const int t[4][4] = {{0, 1, 2, 3}, {1, 4, 5, 6}, {2, 5, 7, 8}, {3, 6, 8, 9}};
-  return t[i][j];
+ACOPF_HD inline T resid_dot2(T r, const T a[4], const T x[4]) {
+  T s = r, e = T(0);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    T pr = -a[j] * x[j];
+    T pe = fma(-a[j], x[j], -pr);  // -a x = pr + pe exactly
+    T t = s + pr;
+    T z = t - s;
+    T se = (s - (t - z)) + (pr - z);  // s + pr = t + se exactly
+    s = t;
+    e += se + pe;
+  }
+  return s + e;
 }
 
-template <typename T>
-struct Eps;
-template <>
-struct Eps<double> {
-  static constexpr double v = 2.2204460492503131e-16;
-};
-template <>
-struct Eps<float> {
-  static constexpr float v = 1.1920928955078125e-07f;
-};
-
 // Box-constrained strictly convex QP  min 1/2 x'Hx + b'x,  lo <= x <= hi,
-// by the primal active-set method from the feasible start x.  fix[i]: 0 free,
-// -1 at lo, +1 at hi.  Returns the number of factorisations used.
+// by the primal active-set method from the feasible start x.  Bit i of fx:
+// variable i held at a bound (at lo when bit i of hiside is clear).  Returns
+// the number of factorisations used.
 template <typename T>
 ACOPF_HD inline int box_qp(const T h[10], const T b[4], const T lo[4], const T hi[4], T x[4], int maxit) {
-  int fix[4];
-  bool perm[4];
+  unsigned fx = 0, hs = 0, perm = 0;
   T scale = T(0);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    perm[i] = !(lo[i] < hi[i]);
-    if (perm[i]) { x[i] = lo[i]; fix[i] = -1; }
-    else if (x[i] <= lo[i]) { x[i] = lo[i]; fix[i] = -1; }
-    else if (x[i] >= hi[i]) { x[i] = hi[i]; fix[i] = 1; }
-    else fix[i] = 0;
+    if (!(lo[i] < hi[i])) { x[i] = lo[i]; fx |= 1u << i; perm |= 1u << i; }
+    else if (x[i] <= lo[i]) { x[i] = lo[i]; fx |= 1u << i; }
+    else if (x[i] >= hi[i]) { x[i] = hi[i]; fx |= 1u << i; hs |= 1u << i; }
     scale = fmax(scale, fabs(b[i]));
   }
   T hmax = T(0);
@@ -131,34 +154,26 @@ ACOPF_HD inline int box_qp(const T h[10], const T b[4], const T lo[4], const T h
   int it = 0;
   for (; it < maxit; ++it) {
     // minimiser over the free variables with the others held at their bounds
-    T hh[10], rhs[4], y[4];
-#pragma unroll
-    for (int k = 0; k < 10; ++k) hh[k] = h[k];
+    const unsigned fr = ~fx & 15u;
+    T rhs[4], y[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      if (fix[i]) {
-        rhs[i] = T(0);
+      T s = -b[i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) hh[pk(i, j)] = T(0);
-        hh[pk(i, i)] = T(1);
-      } else {
-        T s = -b[i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (fix[j]) s -= h[pk(i, j)] * x[j];
-        rhs[i] = s;
-      }
+      for (int j = 0; j < 4; ++j)
+        if ((fx >> j) & 1u) s -= h[pk(i, j)] * x[j];
+      rhs[i] = ((fx >> i) & 1u) ? T(0) : s;
     }
-    if (!chol4_solve(hh, rhs, y)) break;
+    if (!chol4_masked(h, fr, rhs, y)) break;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-      if (fix[i]) y[i] = x[i];
+      if ((fx >> i) & 1u) y[i] = x[i];
     // longest feasible step towards y
     T alpha = T(1);
     int blk = -1, side = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      if (fix[i]) continue;
+      if ((fx >> i) & 1u) continue;
       T dx = y[i] - x[i];
       if (y[i] < lo[i] && dx < T(0)) {
         T a = (lo[i] - x[i]) / dx;
@@ -172,12 +187,13 @@ ACOPF_HD inline int box_qp(const T h[10], const T b[4], const T lo[4], const T h
       alpha = alpha < T(0) ? T(0) : alpha;
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        if (!fix[i]) x[i] = clampv(x[i] + alpha * (y[i] - x[i]), lo[i], hi[i]);
+        if (!((fx >> i) & 1u)) x[i] = clampv(x[i] + alpha * (y[i] - x[i]), lo[i], hi[i]);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
         if (i == blk) {
           x[i] = side < 0 ? lo[i] : hi[i];
-          fix[i] = side;
+          fx |= 1u << i;
+          if (side > 0) hs |= 1u << i; else hs &= ~(1u << i);
         }
       continue;
     }
@@ -197,39 +213,51 @@ ACOPF_HD inline int box_qp(const T h[10], const T b[4], const T lo[4], const T h
     T wv = tol;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      if (!fix[i] || perm[i]) continue;
-      T v = fix[i] < 0 ? -g[i] : g[i];
+      if (!((fx >> i) & 1u) || ((perm >> i) & 1u)) continue;
+      T v = ((hs >> i) & 1u) ? g[i] : -g[i];
       if (v > wv) { wv = v; worst = i; }
     }
     if (worst < 0) {
       if (sizeof(T) < sizeof(double)) {
-        // final active set: one step of iterative refinement with the residual
-        // formed in FP64 (the condition number, rho I against rho F'F, reaches 1e4)
+        // final active set: one step of iterative refinement, the residual of
+        // the reduced system taken in twice the working precision (the
+        // condition number, rho I against rho F'F, reaches 1e4)
         T rr[4], dy[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          double acc = (double)rhs[i];
+          T a[4], xf[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc -= (double)hh[pk(i, j)] * (double)(fix[j] ? T(0) : x[j]);
-          rr[i] = fix[i] ? T(0) : (T)acc;
+          for (int j = 0; j < 4; ++j) {
+            a[j] = h[pk(i, j)];
+            xf[j] = ((fx >> j) & 1u) ? T(0) : x[j];
+          }
+          T ri = resid_dot2(rhs[i], a, xf);
+          rr[i] = ((fx >> i) & 1u) ? T(0) : ri;
         }
-        if (chol4_solve(hh, rr, dy))
+        if (chol4_masked(h, fr, rr, dy))
 #pragma unroll
           for (int i = 0; i < 4; ++i)
-            if (!fix[i]) x[i] = clampv(x[i] + dy[i], lo[i], hi[i]);
+            if (!((fx >> i) & 1u)) x[i] = clampv(x[i] + dy[i], lo[i], hi[i]);
       }
       return it + 1;
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (i == worst) fix[i] = 0;
+    fx &= ~(1u << worst);
+    hs &= ~(1u << worst);
   }
   return it;
 }
 
+// row r of the ALM: h_r(x) (<= 0 when satisfied); rows 2, 3 are the angle rows
 template <typename T>
 ACOPF_HD inline T row_h(const LineQP<T>& P, int r, const T x[4]) {
-  return P.R[r][0] * x[0] + P.R[r][1] * x[1] + P.R[r][2] * x[2] + P.R[r][3] * x[3] - P.rb[r];
+  if (r < 2) return P.R[r][0] * x[0] + P.R[r][1] * x[1] + P.R[r][2] * x[2] + P.R[r][3] * x[3] - P.rb[r];
+  T dth = x[1] - x[3];
+  return r == 2 ? dth - P.ahi : P.alo - dth;
+}
+
+template <typename T>
+ACOPF_HD inline bool row_on(const LineQP<T>& P, int r) {
+  return r < 2 ? P.on[r] : P.ang;
 }
 
 template <typename T>
@@ -240,7 +268,7 @@ ACOPF_HD inline void line_solve(const LineQP<T>& P, T x[4], T u[4], T beta, T al
     unsigned pat = 0;
 #pragma unroll
     for (int r = 0; r < 4; ++r)
-      if (P.on[r] && u[r] + beta * row_h(P, r, x) > T(0)) pat |= 1u << r;
+      if (row_on(P, r) && u[r] + beta * row_h(P, r, x) > T(0)) pat |= 1u << r;
     for (int it = 0; it < newton_max; ++it) {
       // pieces fixed: quadratic beta R R' and linear (u - beta rb) R on the rows in pat
       T h[10], b[4];
@@ -249,7 +277,7 @@ ACOPF_HD inline void line_solve(const LineQP<T>& P, T x[4], T u[4], T beta, T al
 #pragma unroll
       for (int i = 0; i < 4; ++i) b[i] = P.c[i];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < 2; ++r) {
         if (!((pat >> r) & 1u)) continue;
         const T* Rr = P.R[r];
         T lin = u[r] - beta * P.rb[r];
@@ -260,12 +288,23 @@ ACOPF_HD inline void line_solve(const LineQP<T>& P, T x[4], T u[4], T beta, T al
           for (int j = i; j < 4; ++j) h[pk(i, j)] += beta * Rr[i] * Rr[j];
         }
       }
+      // angle rows: R = +-(e1 - e3), right-hand sides ahi and -alo
+      if (pat & 12u) {
+        T lin = (pat & 4u) ? u[2] - beta * P.ahi : -(u[3] + beta * P.alo);
+        T qq = (pat & 4u ? beta : T(0)) + (pat & 8u ? beta : T(0));
+        if ((pat & 12u) == 12u) lin = u[2] - beta * P.ahi - (u[3] + beta * P.alo);
+        b[1] += lin;
+        b[3] -= lin;
+        h[4] += qq;
+        h[9] += qq;
+        h[6] -= qq;
+      }
       int nf = box_qp(h, b, P.lo, P.hi, x, 12);
       if (work) work[0] += nf;
       unsigned np = 0;
 #pragma unroll
       for (int r = 0; r < 4; ++r)
-        if (P.on[r] && u[r] + beta * row_h(P, r, x) > T(0)) np |= 1u << r;
+        if (row_on(P, r) && u[r] + beta * row_h(P, r, x) > T(0)) np |= 1u << r;
       if (np == pat) break;
       pat = np;
     }
@@ -273,7 +312,7 @@ ACOPF_HD inline void line_solve(const LineQP<T>& P, T x[4], T u[4], T beta, T al
     T viol = T(0);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      if (!P.on[r]) {
+      if (!row_on(P, r)) {
         u[r] = T(0);
         continue;
       }

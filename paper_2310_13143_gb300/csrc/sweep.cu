@@ -165,89 +165,95 @@ __device__ __forceinline__ void gen_phase(const SweepP<T>& p, int g, float sc) {
   ((V2<T>*)d.XG)[g] = x;
 }
 
-// One branch's line subproblem.  rsrc points at chunk 0 of the branch's record;
-// chunk c is at rsrc[c * rstride] (global memory: stride L; a shared-memory tile:
-// stride TILE).  z, lambda, u and rho are passed in.
+// Residual balancing changed this branch's penalty by the factor sc:
+// Q = A'HA + rho (F'F + I) and c0 = gH + rho F'f0 change with rho.  The
+// record is updated in place (rs: the branch's chunk 0, stride rstride: global
+// memory or a shared-memory tile) and in global memory; returns the new rho.
+// Out of line: it runs only every rb_period iterations and must not add to
+// the registers of the common path.
 template <typename T>
-__device__ __forceinline__ void line_compute(const SweepP<T>& p, int l, float sc, const V4<T>* rsrc, int rstride,
+__device__ __noinline__ T rb_rescale(const Dev& d, int l, float sc, V4<T>* rs, int rstride, T rho) {
+  T* rt = (T*)rs;
+  auto at = [&](int e) -> T& { return rt[4 * (e >> 2) * rstride + (e & 3)]; };
+  const double r0 = (double)rho;
+  const double dr = r0 * ((double)sc - 1.0);
+  for (int a = 0; a < 4; ++a) {
+    for (int b = a; b < 4; ++b) {
+      double ff = a == b ? 1.0 : 0.0;
+      for (int f = 0; f < 4; ++f) ff += (double)at(10 + 4 * f + a) * (double)at(10 + 4 * f + b);
+      at(pk(a, b)) = (T)((double)at(pk(a, b)) + dr * ff);
+    }
+  }
+  for (int a = 0; a < 4; ++a) {
+    double cf = 0.0;
+    for (int f = 0; f < 4; ++f) cf += (double)at(10 + 4 * f + a) * (double)at(26 + f);
+    at(30 + a) = (T)((double)at(30 + a) + dr * cf);
+  }
+  V4<T>* R = (V4<T>*)d.lrec;
+  const int chunks[5] = {0, 1, 2, 7, 8};
+  for (int k = 0; k < 5; ++k) R[(size_t)chunks[k] * d.L + l] = rs[chunks[k] * rstride];
+  T rn = (T)(r0 * (double)sc);
+  ((T*)d.trho_l)[l] = rn;
+  return rn;
+}
+
+// One branch's line subproblem.  rs points at chunk 0 of the branch's record;
+// chunk c is at rs[c * rstride] (global memory: stride L; a shared-memory tile:
+// stride TILE).  Record values are read where they are used rather than
+// copied to registers, to keep the kernel's register count low.  z, lambda,
+// u and rho are passed in.
+template <typename T>
+__device__ __forceinline__ void line_compute(const SweepP<T>& p, int l, float sc, V4<T>* rs, int rstride,
                                              V4<T> z0, V4<T> z1, V4<T> l0, V4<T> l1, V4<T> uu, T rho) {
   const Dev& d = p.d;
-  const int L = d.L;
-  T rec[56];
-#pragma unroll
-  for (int c = 0; c < kRecChunks; ++c) {
-    V4<T> v = rsrc[c * rstride];
-    rec[4 * c] = v.x;
-    rec[4 * c + 1] = v.y;
-    rec[4 * c + 2] = v.z;
-    rec[4 * c + 3] = v.w;
-  }
-  if (sc != 1.0f) {
-    // residual balancing: Q = A'HA + rho (F'F + I) and c0 = gH + rho F'f0 change with rho
-    V4<T>* R = (V4<T>*)d.lrec;
-    double r0 = (double)rho;
-    double dr = r0 * ((double)sc - 1.0);
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-#pragma unroll
-      for (int b = a; b < 4; ++b) {
-        double ff = a == b ? 1.0 : 0.0;
-#pragma unroll
-        for (int f = 0; f < 4; ++f) ff += (double)rec[10 + 4 * f + a] * (double)rec[10 + 4 * f + b];
-        rec[pk(a, b)] = (T)((double)rec[pk(a, b)] + dr * ff);
-      }
-      double cf = 0.0;
-#pragma unroll
-      for (int f = 0; f < 4; ++f) cf += (double)rec[10 + 4 * f + a] * (double)rec[26 + f];
-      rec[30 + a] = (T)((double)rec[30 + a] + dr * cf);
-    }
-    const int chunks[5] = {0, 1, 2, 7, 8};
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      int c = chunks[k];
-      V4<T> v;
-      v.x = rec[4 * c]; v.y = rec[4 * c + 1]; v.z = rec[4 * c + 2]; v.w = rec[4 * c + 3];
-      R[c * L + l] = v;
-    }
-    rho = (T)(r0 * (double)sc);
-    ((T*)d.trho_l)[l] = rho;
-  }
+  if (sc != 1.0f) rho = rb_rescale(d, l, sc, rs, rstride, rho);
+  const T* rt = (const T*)rs;
+  auto rec = [&](int e) -> T { return rt[4 * (e >> 2) * rstride + (e & 3)]; };
   // couplings: flows p_ij q_ij p_ji q_ji (F rows 0..3), voltages dbar 0..3
-  T zf[4] = {z0.x, z0.y, z1.x, z1.y}, lf[4] = {l0.x, l0.y, l1.x, l1.y};
-  T zv[4] = {z0.z, z0.w, z1.z, z1.w}, lv[4] = {l0.z, l0.w, l1.z, l1.w};
+  const T zf[4] = {z0.x, z0.y, z1.x, z1.y}, lf[4] = {l0.x, l0.y, l1.x, l1.y};
+  const T zv[4] = {z0.z, z0.w, z1.z, z1.w}, lv[4] = {l0.z, l0.w, l1.z, l1.w};
   LineQP<T> P;
 #pragma unroll
-  for (int k = 0; k < 10; ++k) P.q[k] = rec[k];
+  for (int k = 0; k < 10; ++k) P.q[k] = rec(k);
+  // c = c0 + F'(lambda_F - rho z_F) + lambda_V - rho z_V
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    T s = rec[30 + i] + lv[i] - rho * zv[i];
+    T s = rec(30 + i) + lv[i] - rho * zv[i];
 #pragma unroll
-    for (int f = 0; f < 4; ++f) s += rec[10 + 4 * f + i] * (lf[f] - rho * zf[f]);
+    for (int f = 0; f < 4; ++f) s += rec(10 + 4 * f + i) * (lf[f] - rho * zf[f]);
     P.c[i] = s;
-    P.lo[i] = rec[34 + i];
-    P.hi[i] = rec[38 + i];
+    P.lo[i] = rec(34 + i);
+    P.hi[i] = rec(38 + i);
   }
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) P.R[e][i] = rec[42 + 4 * e + i];
-    P.rb[e] = rec[50 + e];
-    P.on[e] = rec[54 + e] > T(0);
+    for (int i = 0; i < 4; ++i) P.R[e][i] = rec(42 + 4 * e + i);
+    P.rb[e] = rec(50 + e);
+    P.on[e] = rec(54 + e) > T(0);
   }
-  T alo = rec[52], ahi = rec[53];
-  bool ang = ahi < T(1e29);
-  P.R[2][0] = T(0); P.R[2][1] = T(1); P.R[2][2] = T(0); P.R[2][3] = T(-1); P.rb[2] = ahi; P.on[2] = ang;
-  P.R[3][0] = T(0); P.R[3][1] = T(-1); P.R[3][2] = T(0); P.R[3][3] = T(1); P.rb[3] = -alo; P.on[3] = ang;
+  P.alo = rec(52);
+  P.ahi = rec(53);
+  P.ang = P.ahi < T(1e29);
   T x[4], u[4] = {uu.x, uu.y, uu.z, uu.w};
 #pragma unroll
   for (int i = 0; i < 4; ++i) x[i] = clampv(zv[i], P.lo[i], P.hi[i]);
   T qd = fmax(fmax(P.q[0], P.q[4]), fmax(P.q[7], P.q[9]));
   line_solve(P, x, u, p.beta_scale * qd, p.alm_tol, p.alm_outer, p.newton_max);
+  // flows at the solution; F and f0 are read again (volatile: not held in
+  // registers across the solve)
+  const volatile T* rv = rt;
   T xf[4];
 #pragma unroll
-  for (int f = 0; f < 4; ++f)
-    xf[f] = rec[10 + 4 * f] * x[0] + rec[10 + 4 * f + 1] * x[1] + rec[10 + 4 * f + 2] * x[2] +
-            rec[10 + 4 * f + 3] * x[3] + rec[26 + f];
+  for (int f = 0; f < 4; ++f) {
+    T s = rv[4 * ((26 + f) >> 2) * rstride + ((26 + f) & 3)];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = 10 + 4 * f + i;
+      s += rv[4 * (e >> 2) * rstride + (e & 3)] * x[i];
+    }
+    xf[f] = s;
+  }
   V4<T>* X = (V4<T>*)d.X;
   V4<T> o0, o1, ou;
   o0.x = xf[0]; o0.y = xf[1]; o0.z = x[0]; o0.w = x[1];
@@ -264,7 +270,7 @@ __device__ __forceinline__ void line_phase(const SweepP<T>& p, int l, float sc) 
   const Dev& d = p.d;
   const V4<T>* Z = (const V4<T>*)d.Z;
   const V4<T>* LM = (const V4<T>*)d.LAM;
-  line_compute(p, l, sc, (const V4<T>*)d.lrec + l, d.L, Z[2 * l], Z[2 * l + 1], LM[2 * l], LM[2 * l + 1],
+  line_compute(p, l, sc, (V4<T>*)d.lrec + l, d.L, Z[2 * l], Z[2 * l + 1], LM[2 * l], LM[2 * l + 1],
                ((const V4<T>*)d.U)[l], ((const T*)d.trho_l)[l]);
 }
 

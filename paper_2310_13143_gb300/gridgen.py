@@ -362,16 +362,53 @@ def tree_plus_grid(nbus: int, nextra: int, ngen: int, nload: int, seed: int, nam
     return _assemble(nbus, edges, ngen, nload, rng, xy=xy, name=name or f"tree{nbus}-s{seed}", spread=False)
 
 
+def _morton(xy: np.ndarray) -> np.ndarray:
+    """Z-order (Morton) keys of points in [0,1]^2: 16-bit coordinates with
+    their bits interleaved."""
+    q = np.clip((xy * 65535.0).astype(np.uint64), 0, 65535)
+
+    def spread(v):
+        v = (v | (v << 8)) & np.uint64(0x00FF00FF)
+        v = (v | (v << 4)) & np.uint64(0x0F0F0F0F)
+        v = (v | (v << 2)) & np.uint64(0x33333333)
+        v = (v | (v << 1)) & np.uint64(0x55555555)
+        return v
+
+    return spread(q[:, 0]) | (spread(q[:, 1]) << np.uint64(1))
+
+
+def relabel_regional(g: Grid) -> Grid:
+    """The same grid with buses numbered along a Z-order curve of their
+    coordinates and branches sorted by (lower, higher) end bus, so that buses
+    close in the plane, and the branches between them, are close in every
+    array (regional numbering, as in published grid cases).  Generators keep
+    their order; only labels change."""
+    if g.xy is None:
+        return g
+    perm = np.argsort(_morton(g.xy), kind="stable")      # new bus -> old bus
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(g.nbus)
+    f = inv[g.f].astype(np.int32)
+    t = inv[g.t].astype(np.int32)
+    border = np.lexsort((np.maximum(f, t), np.minimum(f, t)))
+    bus = {k: getattr(g, k)[perm] for k in ("bus_type", "pd", "qd", "gs", "bs", "vmin", "vmax")}
+    br = {k: getattr(g, k)[border] for k in ("r", "x", "b", "rate", "angmin", "angmax", "tap", "shift")}
+    return replace(g, **bus, **br, f=f[border], t=t[border], gbus=inv[g.gbus].astype(np.int32), xy=g.xy[perm])
+
+
 def geometric_grid(nbus: int, seed: int, nbranch: int | None = None, ngen: int | None = None,
-                   nload: int | None = None, name: str = "") -> Grid:
-    """Random geometric graph on U[0,1]^2 with mean degree 2*nbranch/nbus."""
+                   nload: int | None = None, name: str = "", regional: bool = True) -> Grid:
+    """Random geometric graph on U[0,1]^2 with mean degree 2*nbranch/nbus.
+    With regional=True (default) the grid is relabelled by relabel_regional;
+    regional=False keeps the labels of the construction (random in the plane)."""
     rng = np.random.default_rng(seed)
     nbranch = int(round(1.35 * nbus)) if nbranch is None else nbranch
     ngen = max(2, int(round(0.2 * nbus))) if ngen is None else ngen
     nload = int(round(0.6 * nbus)) if nload is None else nload
     xy = rng.random((nbus, 2))
     edges = _geometric_edges(xy, nbranch, rng)
-    return _assemble(nbus, edges, ngen, nload, rng, xy=xy, name=name or f"geo{nbus}-s{seed}", vband=(0.9, 1.1))
+    g = _assemble(nbus, edges, ngen, nload, rng, xy=xy, name=name or f"geo{nbus}-s{seed}", vband=(0.9, 1.1))
+    return relabel_regional(g) if regional else g
 
 
 # --------------------------------------------------------------------------
@@ -416,9 +453,9 @@ def grid_30bus(seed: int = 3) -> Grid:
     return tree_plus_grid(30, 12, 6, 20, seed, name=f"syn30-s{seed}")
 
 
-def grid_2000bus(seed: int = 2) -> Grid:
+def grid_2000bus(seed: int = 2, regional: bool = True) -> Grid:
     """2,000 buses, about 2,700 branches (mean degree 2.7), 400 generators, 1,200 loads."""
-    return geometric_grid(2000, seed, name=f"syn2000-s{seed}")
+    return geometric_grid(2000, seed, name=f"syn2000-s{seed}", regional=regional)
 
 
 def grid_70k(seed: int = 5) -> Grid:
@@ -426,15 +463,16 @@ def grid_70k(seed: int = 5) -> Grid:
     return geometric_grid(70000, seed, nbranch=90000, ngen=10000, nload=40000, name=f"syn70k-s{seed}")
 
 
-def batched_uneven(seed: int = 3, nscen: int = 256, ngrids: int = 64, base: Grid | None = None):
+def batched_uneven(seed: int = 3, nscen: int = 256, ngrids: int = 64, base: Grid | None = None,
+                   regional: bool = True):
     """256 correlated load scenarios of the 2,000-bus grid plus 64 grids whose bus
     counts are log-uniform in [118, 10000]."""
-    base = grid_2000bus() if base is None else base
+    base = grid_2000bus(regional=regional) if base is None else base
     out = scenarios_cholesky(base, nscen, seed=1000 + seed)
     rng = np.random.default_rng(seed)
     sizes = np.round(np.exp(rng.uniform(math.log(118), math.log(10000), ngrids))).astype(int)
     for k, nb in enumerate(sizes):
-        out.append(geometric_grid(int(nb), seed=10_000 + 97 * seed + k))
+        out.append(geometric_grid(int(nb), seed=10_000 + 97 * seed + k, regional=regional))
     return out
 
 

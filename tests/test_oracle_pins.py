@@ -575,3 +575,17 @@ def test_sqp_multipliers_are_marginal_costs():
     np.testing.assert_allclose(st["nu"][:, 0], -mc, rtol=1e-5)
     p, dd = m.kkt(x, r["pi"], st["nu"].ravel(), st["ul"].ravel())
     assert p < 1e-7 and dd < 1e-6
+
+
+def test_sqp_objective_is_invariant_under_relabelling():
+    """Renumbering buses and reordering branches describes the same grid, so
+    the SQP solution's objective and infeasibility must not change (beyond
+    rounding): an index mix-up between bus, branch or generator arrays in the
+    oracle would break this."""
+    a = gg.geometric_grid(118, seed=11, regional=False)
+    b = gg.relabel_regional(a)
+    assert not np.array_equal(a.f, b.f)
+    ra = oracle.Model(a).sqp(oracle.SqpOptions())
+    rb = oracle.Model(b).sqp(oracle.SqpOptions())
+    assert abs(ra["obj"] - rb["obj"]) <= 1e-9 * abs(ra["obj"])
+    assert rb["primal"] <= 1e-4
