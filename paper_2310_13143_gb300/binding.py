@@ -15,6 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libacopf.so")
 
 DP = C.POINTER(C.c_double)
+FP = C.POINTER(C.c_float)
 IP = C.POINTER(C.c_int32)
 
 ACOPF_FP64, ACOPF_MIXED = 0, 1
@@ -123,6 +124,22 @@ def lib():
             "acopf_get_profile_phases": (S, [H, DP]),
             "acopf_tune": (S, [H, C.c_int32, C.c_int32, C.c_int32]),
             "acopf_get_profile": (S, [H, DP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+            "acopf_set_warm_start_device": (S, [H, C.c_void_p, C.c_int64, C.c_double, S, S, S, S]),
+            "acopf_mlp_create": (S, [IP, C.c_int32, C.c_int32, C.c_int32, C.POINTER(H)]),
+            "acopf_mlp_destroy": (S, [H]),
+            "acopf_mlp_set_stream": (S, [H, C.c_void_p]),
+            "acopf_mlp_last_error": (S, [H, C.c_char_p, C.c_size_t]),
+            "acopf_mlp_num_params": (S, [H, C.POINTER(C.c_int64)]),
+            "acopf_mlp_set_params": (S, [H, FP, C.c_int64]),
+            "acopf_mlp_get_params": (S, [H, FP, C.c_int64]),
+            "acopf_mlp_get_grads": (S, [H, FP, C.c_int64]),
+            "acopf_mlp_fit_standardiser": (S, [H, C.c_void_p, C.c_void_p, C.c_int32]),
+            "acopf_mlp_get_standardiser": (S, [H, FP, FP, FP, FP]),
+            "acopf_mlp_forward": (S, [H, C.c_void_p, C.c_int32, C.c_void_p]),
+            "acopf_mlp_train_step": (S, [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p]),
+            "acopf_mlp_sync": (S, [H]),
+            "acopf_gemm_bf16": (S, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                    C.c_void_p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -138,7 +155,11 @@ EXPORTED = ["acopf_default_options", "admm_default_options", "sqp_default_option
             "acopf_set_iterate", "acopf_get_iterate", "acopf_build_qp", "acopf_get_qp", "acopf_get_admm_state",
             "acopf_set_admm_state", "admm_iterate", "acopf_get_step", "acopf_launch_count", "acopf_profile",
             "acopf_get_profile", "acopf_get_history", "admm_iterate_static", "acopf_get_profile_phases",
-            "acopf_tune"]
+            "acopf_tune", "acopf_set_warm_start_device", "acopf_mlp_create", "acopf_mlp_destroy",
+            "acopf_mlp_set_stream", "acopf_mlp_last_error", "acopf_mlp_num_params", "acopf_mlp_set_params",
+            "acopf_mlp_get_params", "acopf_mlp_get_grads", "acopf_mlp_fit_standardiser",
+            "acopf_mlp_get_standardiser", "acopf_mlp_forward", "acopf_mlp_train_step", "acopf_mlp_sync",
+            "acopf_gemm_bf16"]
 
 
 def _dp(a):
@@ -252,6 +273,12 @@ class Solver:
     def build_qp(self, delta=1.0, rho=2e4, use_angle=True):
         self._check(lib().acopf_build_qp(self.h, float(delta), float(rho), int(bool(use_angle))))
 
+    def set_warm_start_device(self, pred_ptr: int, ld: int, base_rho=2e4, use_x=True, use_pi=True, use_lambda=True,
+                              use_rho=True):
+        """Warm start of every instance from device predictions (FP32 [K x ld] at pred_ptr)."""
+        self._check(lib().acopf_set_warm_start_device(self.h, C.c_void_p(pred_ptr), int(ld), float(base_rho),
+                                                      int(use_x), int(use_pi), int(use_lambda), int(use_rho)))
+
     def set_warm_start(self, inst, x0=None, lambda0=None, rho=None):
         a, b, c = (None if v is None else _f64(v) for v in (x0, lambda0, rho))
         self._check(lib().acopf_set_warm_start(self.h, inst, _dp(a), _dp(b), _dp(c)))
@@ -356,3 +383,83 @@ class Solver:
         n = C.c_int64()
         self._check(lib().acopf_launch_count(self.h, C.byref(n)))
         return n.value
+
+
+def gemm_bf16(a_ptr: int, b_ptr: int, c_ptr: int, M: int, N: int, K: int, splits: int = 1, stream: int = 0):
+    """C [M x N] = A [M x K] B [N x K]^T on the tensor cores (device pointers:
+    bfloat16 A and B, FP32 C)."""
+    st = lib().acopf_gemm_bf16(C.c_void_p(a_ptr), C.c_void_p(b_ptr), C.c_void_p(c_ptr), M, N, K, splits,
+                               C.c_void_p(stream))
+    if st != 0:
+        raise AcopfError(st, "acopf_gemm_bf16 failed")
+
+
+class Mlp:
+    """The warm-start network (include/acopf_mlp.h); device buffers are passed
+    as integer device pointers."""
+
+    def __init__(self, dims, max_batch: int, device: int = 0):
+        self.dims = [int(d) for d in dims]
+        arr = np.ascontiguousarray(self.dims, dtype=np.int32)
+        h = C.c_void_p()
+        st = lib().acopf_mlp_create(arr.ctypes.data_as(IP), len(self.dims) - 1, int(max_batch), device, C.byref(h))
+        if st != 0:
+            raise AcopfError(st, "acopf_mlp_create failed")
+        self.h = h
+        n = C.c_int64()
+        self._check(lib().acopf_mlp_num_params(self.h, C.byref(n)))
+        self.nparams = n.value
+
+    def _check(self, st):
+        if st != 0:
+            buf = C.create_string_buffer(512)
+            lib().acopf_mlp_last_error(self.h, buf, 512)
+            raise AcopfError(st, buf.value.decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().acopf_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_ptr: int):
+        self._check(lib().acopf_mlp_set_stream(self.h, C.c_void_p(stream_ptr)))
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        self._check(lib().acopf_mlp_set_params(self.h, a.ctypes.data_as(FP), a.size))
+
+    def get_params(self):
+        a = np.zeros(self.nparams, dtype=np.float32)
+        self._check(lib().acopf_mlp_get_params(self.h, a.ctypes.data_as(FP), a.size))
+        return a
+
+    def get_grads(self):
+        a = np.zeros(self.nparams, dtype=np.float32)
+        self._check(lib().acopf_mlp_get_grads(self.h, a.ctypes.data_as(FP), a.size))
+        return a
+
+    def fit_standardiser(self, x_ptr: int, y_ptr: int, rows: int):
+        self._check(lib().acopf_mlp_fit_standardiser(self.h, C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(rows)))
+
+    def get_standardiser(self):
+        d0, dn = self.dims[0], self.dims[-1]
+        out = [np.zeros(d, dtype=np.float32) for d in (d0, d0, dn, dn)]
+        self._check(lib().acopf_mlp_get_standardiser(self.h, *[o.ctypes.data_as(FP) for o in out]))
+        return out
+
+    def forward(self, x_ptr: int, rows: int, y_ptr: int):
+        self._check(lib().acopf_mlp_forward(self.h, C.c_void_p(x_ptr), int(rows), C.c_void_p(y_ptr)))
+
+    def train_step(self, x_ptr: int, t_ptr: int, idx_ptr, rows: int, lr: float, loss_ptr=None):
+        self._check(lib().acopf_mlp_train_step(self.h, C.c_void_p(x_ptr), C.c_void_p(t_ptr),
+                                               C.c_void_p(idx_ptr or 0) if idx_ptr else None, int(rows),
+                                               float(lr), C.c_void_p(loss_ptr) if loss_ptr else None))
+
+    def sync(self):
+        self._check(lib().acopf_mlp_sync(self.h))

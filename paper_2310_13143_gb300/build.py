@@ -12,7 +12,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libacopf.so")
-SOURCES = ["api.cu", "sqp_kernels.cu", "sweep.cu"]
+SOURCES = ["api.cu", "sqp_kernels.cu", "sweep.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 
@@ -29,7 +29,7 @@ def _stale() -> bool:
         return True
     t = os.path.getmtime(OUT)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    deps.append(os.path.join(HERE, "..", "include", "acopf.h"))
+    deps += [os.path.join(HERE, "..", "include", f) for f in ("acopf.h", "acopf_mlp.h")]
     return any(os.path.getmtime(p) > t for p in deps if os.path.exists(p))
 
 

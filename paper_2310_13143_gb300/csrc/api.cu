@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "../../include/acopf_mlp.h"
 
 namespace acopf {
 void launch_admittance(Ctx& c, const double* r, const double* x, const double* b, const double* tap,
@@ -971,6 +972,33 @@ acopf_status acopf_set_warm_start(acopf_handle h, int32_t inst, const double* x0
     CK(cudaMemcpy(c->d.rho_g + g0, rg.data(), sizeof(double) * ng, cudaMemcpyHostToDevice));
     c->warm_rho = true;
   }
+  return ACOPF_OK;
+}
+
+acopf_status acopf_set_warm_start_device(acopf_handle h, const float* pred, int64_t ld, double base_rho,
+                                         int32_t use_x, int32_t use_pi, int32_t use_lambda, int32_t use_rho) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !pred || (use_rho && !(base_rho > 0)) || (use_pi && !use_x))
+    return fail(c, ACOPF_EINVAL, "acopf_set_warm_start_device: bad arguments");
+  const int K = c->d.K;
+  const int nb = c->h_bus_off[1] - c->h_bus_off[0];
+  const int nl = c->h_br_off[1] - c->h_br_off[0];
+  const int ng = c->h_gen_off[1] - c->h_gen_off[0];
+  for (int k = 1; k < K; ++k)
+    if (c->h_bus_off[k + 1] - c->h_bus_off[k] != nb || c->h_br_off[k + 1] - c->h_br_off[k] != nl ||
+        c->h_gen_off[k + 1] - c->h_gen_off[k] != ng)
+      return fail(c, ACOPF_EINVAL, "acopf_set_warm_start_device: instances of different sizes");
+  const int64_t width = 5LL * ng + 2LL * nb + 15LL * nl;
+  if (ld < width) return fail(c, ACOPF_EINVAL, "acopf_set_warm_start_device: ld below the row width 5G + 2B + 15L");
+  if (!c->d_gen_iperm) {
+    CK(dalloc(c, &c->d_gen_iperm, (size_t)c->d.G));
+    CK(upload(c, c->d_gen_iperm, c->h_gen_iperm, (size_t)c->d.G));
+  }
+  launch_warm_scatter(*c, pred, ld, nb, nl, ng, base_rho, use_x, use_pi, use_lambda, use_rho);
+  CK(cudaGetLastError());
+  if (use_x) c->warm_x = true;
+  if (use_lambda) c->warm_lam = true;
+  if (use_rho) c->warm_rho = true;
   return ACOPF_OK;
 }
 

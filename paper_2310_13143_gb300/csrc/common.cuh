@@ -146,8 +146,9 @@ struct Ctx {
   double prof_ms = 0.0;
   int64_t prof_sweeps = 0, prof_iters = 0;
   int sweep_stages = 2;  // FP32 sweep: branch-tile buffers per CTA (1 or 2)
-  // warm start staged by acopf_set_warm_start
+  // warm start staged by acopf_set_warm_start / acopf_set_warm_start_device
   bool warm_x = false, warm_lam = false, warm_rho = false;
+  int* d_gen_iperm = nullptr;  // device copy of h_gen_iperm (allocated on first use)
 };
 
 // kernels, launchers (defined in the .cu files)
@@ -161,6 +162,8 @@ void launch_merit(Ctx& c);
 void launch_accept_and_kkt(Ctx& c);
 void launch_fill_rho(Ctx& c, double rho);
 void launch_commit_rho(Ctx& c);
+void launch_warm_scatter(Ctx& c, const float* pred, long long ld, int nb, int nl, int ng, double base_rho, int use_x,
+                         int use_pi, int use_lam, int use_rho);
 
 inline unsigned nblk(long n, int t) { return (unsigned)((n + t - 1) / t); }
 

@@ -901,6 +901,69 @@ static inline unsigned cover(const Dev& d) {
   return nblk(m, 256);
 }
 
+// Warm start of every instance from a prediction row per instance (layout of
+// acopf_set_warm_start_device): NLP point clamped into its bounds, line
+// multipliers pi, ADMM multipliers in the sweep precision, per-component
+// penalties.  Grid (ceil(max(B, L, G) / 256), K).
+template <typename T>
+__global__ void k_warm_scatter(Dev d, const float* pred, long long ld, const int* gen_iperm, int nb, int nl, int ng,
+                               double base_rho, int use_x, int use_pi, int use_lam, int use_rho) {
+  const int k = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const float* p = pred + (size_t)k * (size_t)ld;
+  const int b0 = d.bus_off[k], l0 = d.br_off[k], g0 = d.gen_off[k];
+  const int opi = 2 * ng + 2 * nb + 2 * nl, olam = opi + 4 * nl, orho = olam + 8 * nl + 2 * ng;
+  if (use_x) {
+    if (j < ng) {
+      const int g = gen_iperm[g0 + j];
+      d.pg[g] = fmin(fmax((double)p[j], d.pmin[g]), d.pmax[g]);
+      d.qg[g] = fmin(fmax((double)p[ng + j], d.qmin[g]), d.qmax[g]);
+    }
+    if (j < nb) {
+      const int i = b0 + j;
+      d.w[i] = fmin(fmax((double)p[2 * ng + j], d.wmin[i]), d.wmax[i]);
+      d.th[i] = d.isref[i] ? 0.0 : (double)p[2 * ng + nb + j];
+    }
+    if (j < nl) {
+      d.wr[l0 + j] = (double)p[2 * ng + 2 * nb + j];
+      d.wi[l0 + j] = (double)p[2 * ng + 2 * nb + nl + j];
+      for (int r = 0; r < 4; ++r) d.pi[(size_t)r * d.L + l0 + j] = use_pi ? (double)p[opi + 4 * j + r] : 0.0;
+    }
+  }
+  if (use_lam) {
+    if (j < nl) {
+      const float* q = p + olam + 8 * j;  // p_ij q_ij p_ji q_ji w_i th_i w_j th_j
+      V4<T> e0 = {(T)q[0], (T)q[1], (T)q[4], (T)q[5]};
+      V4<T> e1 = {(T)q[2], (T)q[3], (T)q[6], (T)q[7]};
+      ((V4<T>*)d.LAM)[2 * (l0 + j)] = e0;
+      ((V4<T>*)d.LAM)[2 * (l0 + j) + 1] = e1;
+    }
+    if (j < ng) {
+      const int g = gen_iperm[g0 + j];
+      V2<T> v = {(T)p[olam + 8 * nl + 2 * j], (T)p[olam + 8 * nl + 2 * j + 1]};
+      ((V2<T>*)d.LG)[g] = v;
+    }
+  }
+  if (use_rho) {
+    if (j < nl) d.rho_l[l0 + j] = base_rho * exp(fmin(fmax((double)p[orho + j], -2.3), 2.3));
+    if (j < ng) d.rho_g[gen_iperm[g0 + j]] = base_rho * exp(fmin(fmax((double)p[orho + nl + j], -2.3), 2.3));
+  }
+}
+
+void launch_warm_scatter(Ctx& c, const float* pred, long long ld, int nb, int nl, int ng, double base_rho, int use_x,
+                         int use_pi, int use_lam, int use_rho) {
+  int m = nb > nl ? nb : nl;
+  m = m > ng ? m : ng;
+  dim3 grid(nblk(m, 256), c.d.K);
+  if (c.precision == ACOPF_MIXED)
+    k_warm_scatter<float><<<grid, 256, 0, c.stream>>>(c.d, pred, ld, c.d_gen_iperm, nb, nl, ng, base_rho, use_x,
+                                                       use_pi, use_lam, use_rho);
+  else
+    k_warm_scatter<double><<<grid, 256, 0, c.stream>>>(c.d, pred, ld, c.d_gen_iperm, nb, nl, ng, base_rho, use_x,
+                                                        use_pi, use_lam, use_rho);
+  c.launches++;
+}
+
 void launch_flat_start(Ctx& c) {
   k_flat_start<<<cover(c.d), 256, 0, c.stream>>>(c.d);
   c.launches++;

@@ -491,3 +491,18 @@ def two_bus(lossless: bool = True, rate: float = 5.0, pd2: float = 0.8, qd2: flo
         gbus=np.array([0, 1], dtype=np.int32), pmin=np.zeros(2), pmax=np.array(pmax, float),
         qmin=-np.ones(2), qmax=np.ones(2), c2=np.array(c2, float), c1=np.array(c1, float),
         c0=np.zeros(2), base_mva=100.0, xy=np.array([[0.0, 0.0], [1.0, 0.0]]), name="two-bus")
+
+
+# --------------------------------------------------------------------------
+# warm-start network: initial weights
+# --------------------------------------------------------------------------
+def mlp_init(dims, seed: int) -> np.ndarray:
+    """Initial parameters of a network with layer widths dims, as one FP32
+    array (per layer W [out x in] row-major, then b): W ~ N(0, 1/in) (LeCun
+    normal), b = 0."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for i in range(len(dims) - 1):
+        parts.append((rng.standard_normal((dims[i + 1], dims[i])) / math.sqrt(dims[i])).ravel())
+        parts.append(np.zeros(dims[i + 1]))
+    return np.concatenate(parts).astype(np.float32)

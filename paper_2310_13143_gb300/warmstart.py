@@ -1,0 +1,94 @@
+"""Learned warm start of the SQP-ADMM solver (driver over the C ABI).
+
+A network maps a scenario's loads (pd, qd of every bus) to the starting
+point of a solve: the NLP point x0, the line multipliers pi, the ADMM
+multipliers lambda of the first QP and a log penalty factor per component
+(layout of acopf_set_warm_start_device).  The training targets are the
+final iterate, multipliers and ADMM state of cold-start solves of sampled
+scenarios, computed by the same solver; a warm-started solve must still pass
+the solver's own convergence test, so the cold-start method remains the
+judge of the prediction's error.
+
+Everything numeric runs in the library's kernels (solves, tensor-core
+products, Adam, the scatter into the solver); this module only moves arrays
+between calls and draws the mini-batch order.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import binding
+
+
+def output_width(grid) -> int:
+    """5G + 2B + 15L: x0 (2G + 2B + 2L), pi (4L), lambda (8L + 2G), log factor (L + G)."""
+    return 5 * grid.ngen + 2 * grid.nbus + 15 * grid.nbranch
+
+
+def pad8(n: int) -> int:
+    return (n + 7) // 8 * 8
+
+
+def dims_for(grid, hidden=(512, 512, 512)):
+    return [pad8(2 * grid.nbus), *hidden, pad8(output_width(grid))]
+
+
+def loads_matrix(grids, width=None):
+    """Network inputs: [pd | qd] per scenario (zero padded to width)."""
+    w = width or pad8(2 * grids[0].nbus)
+    X = np.zeros((len(grids), w), dtype=np.float32)
+    for k, g in enumerate(grids):
+        X[k, :g.nbus] = g.pd
+        X[k, g.nbus:2 * g.nbus] = g.qd
+    return X
+
+
+def solve_targets(grids, opts, precision="mixed", chunk=256, base_rho=2e4):
+    """Cold-start solves of the scenarios, chunk instances per launch.
+    Returns (targets [n x padded width] FP32, converged flags, ADMM iterations,
+    objectives)."""
+    g0 = grids[0]
+    B, L, G = g0.nbus, g0.nbranch, g0.ngen
+    width = pad8(output_width(g0))
+    T = np.zeros((len(grids), width), dtype=np.float32)
+    conv = np.zeros(len(grids), dtype=bool)
+    iters = np.zeros(len(grids), dtype=np.int64)
+    objs = np.zeros(len(grids))
+    for c0 in range(0, len(grids), chunk):
+        part = grids[c0:c0 + chunk]
+        s = binding.Solver(part, precision=precision)
+        s.sqp_solve(opts)
+        for k in range(len(part)):
+            x, pi = s.get_iterate(k)
+            st = s.get_admm_state(k)
+            r = s.get_residuals(k)
+            row = T[c0 + k]
+            o = 0
+            row[o:o + x.size] = x; o += x.size
+            row[o:o + 4 * L] = pi.ravel(); o += 4 * L
+            row[o:o + 8 * L] = st["lam"].ravel(); o += 8 * L
+            row[o:o + 2 * G] = st["lg"].ravel(); o += 2 * G
+            row[o:o + L + G] = 0.0  # the data-generating solves use one fixed penalty
+            conv[c0 + k] = r["result_name"] == "converged"
+            iters[c0 + k] = r["admm_iter"]
+            objs[c0 + k] = s.get_solution(k)["obj"]
+        s.close()
+    return T, conv, iters, objs
+
+
+def train(net, X_dev, T_dev, n: int, steps: int, batch: int, lr: float, seed: int, stream=None):
+    """Mini-batch Adam on rows [0, n) of the device data set; returns the
+    loss of every step (read back once at the end)."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    dev = X_dev.device
+    losses = torch.zeros(steps, dtype=torch.float32, device=dev)
+    order = np.concatenate([rng.permutation(n) for _ in range((steps * batch) // n + 1)]).astype(np.int32)
+    idx_all = torch.from_numpy(order).to(dev)
+    for k in range(steps):
+        idx = idx_all[k * batch:(k + 1) * batch]
+        net.train_step(X_dev.data_ptr(), T_dev.data_ptr(), idx.data_ptr(), batch, lr,
+                       losses.data_ptr() + 4 * k)
+    net.sync()
+    return losses.cpu().numpy()

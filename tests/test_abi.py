@@ -1,4 +1,4 @@
-"""The C-ABI library loads, exports every entry point include/acopf.h
+"""The C-ABI library loads, exports every entry point include/*.h
 declares, validates its inputs on the host, and fails loudly (no CPU
 fallback) when no CUDA device is present.  No compute call needs a GPU here."""
 import ctypes as C
@@ -21,7 +21,8 @@ def lib():
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "acopf.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = re.findall(r"^\s*(?:acopf_status|void|const char\*)\s+(\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
