@@ -266,12 +266,175 @@ def run_gpu(args, rank, world, local_rank):
                              "objective": plain["obj"], "objective_rel_diff_vs_mixed": abs(plain["obj"] - m["obj"]) / abs(plain["obj"]),
                              "avg_sweep_launch_ms": plain["prof"]["sweep_ms"] / max(plain["prof"]["sweeps"], 1)}
     if world == 1 and not args.no_batched:
-        out["batched_sweep"] = sweep_only(workload_grids("batched"), args.precision, 50, 3, 1)
+        bgrids = workload_grids("batched")
+        out["batched_sweep"] = sweep_only(bgrids, args.precision, 50, 3, 1)
         out["batched_sweep"]["workload"] = ("256 correlated load scenarios of the 2,000-bus grid + 64 grids of "
                                             "118-10,000 buses (log-uniform), one persistent launch, ADMM sweep only")
+        out["batched_solve"] = batched_solve(bgrids)
+    if world == 1 and not args.no_learned:
+        out["learned_warm_start"] = learned_warm_start(args)
+    if world == 1 and not args.no_large:
+        out["large_70k_x16"] = sweep_only(workload_grids("syn70k_x16"), "mixed", 30, 2, 1)
+        out["large_70k_x16"]["workload"] = ("16 correlated load scenarios of a 70,000-bus grid (90,000 branches, "
+                                            "10,000 generators) in one persistent launch, ADMM sweep only")
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(grid, iters_all / max(args.steps, 1), args.cpu_seconds)
     return out
+
+
+def batched_solve(grids, plain_sample=8):
+    """Config 3 solved to the end: every instance of the uneven batch in one
+    handle (launch shape from the autotuner, SQP loop replayed from a CUDA
+    graph), against a plain sample of the same instances solved one at a
+    time, cold, in FP64."""
+    import torch
+
+    from paper_2310_13143_gb300 import binding
+
+    opts = solver_options(binding, "mixed")
+    stream = torch.cuda.Stream()
+    free0 = torch.cuda.mem_get_info()[0]
+    s = binding.Solver(grids, precision="mixed")
+    s.set_stream(stream.cuda_stream)
+    torch.cuda.synchronize()
+    footprint = free0 - torch.cuda.mem_get_info()[0]
+    cache = os.path.join(tempfile.gettempdir(), "acopf_tune_cache.json")
+    shape, tune_us = s.autotune(cache, iters=30)
+    s.sqp_solve_graph(opts, check_every=2)  # warm-up (captures the graph)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.sqp_solve_graph(opts, check_every=2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    rs = [s.get_residuals(k) for k in range(len(grids))]
+    ok = [r["result_name"] == "converged" and r["primal"] <= 1e-4 and r["dual"] <= 1e-4 for r in rs]
+    s.close()
+    # plain: a sample of the same instances, one handle each, cold, FP64
+    idx = list(range(0, len(grids), max(1, len(grids) // plain_sample)))[:plain_sample]
+    pt, pconv = 0.0, 0
+    popts = solver_options(binding, "fp64")
+    for i in idx:
+        p = binding.Solver([grids[i]], precision="fp64")
+        p.set_stream(stream.cuda_stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        p.sqp_solve(popts)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pt += a.elapsed_time(b) / 1e3
+        r = p.get_residuals(0)
+        pconv += int(r["result_name"] == "converged" and r["primal"] <= 1e-4 and r["dual"] <= 1e-4)
+        p.close()
+    sizes = [grids[i].nbus for i in idx]
+    return {"instances": len(grids), "converged": int(sum(ok)), "seconds": t,
+            "value": sum(ok) / t, "unit": "solves/s",
+            "instances_per_s": len(grids) / t,
+            "sqp_iters_max": max(r["sqp_iter"] for r in rs),
+            "admm_iters_mean": float(sum(r["admm_iter"] for r in rs) / len(rs)),
+            "launch_shape": {"block_threads": shape[0], "ctas_per_sm": shape[1], "stages": shape[2],
+                             "tuned_us_per_iter": tune_us},
+            "device_bytes": int(footprint),
+            "plain_fp64_sample": {"instances": len(idx), "buses": sizes, "converged": pconv, "seconds": pt,
+                                  "value": pconv / pt if pt > 0 else 0.0, "unit": "solves/s",
+                                  "instances_per_s": len(idx) / pt if pt > 0 else 0.0},
+            "batched_vs_plain_instances_per_s": (len(grids) / t) / (len(idx) / pt) if pt > 0 else None,
+            "workload": "256 correlated load scenarios of the 2,000-bus grid + 64 grids of 118-10,000 buses, "
+                        "one handle, SQP to 1e-4 (max 40 SQP iterations, 1,000 ADMM iterations per QP)"}
+
+
+def learned_warm_start(args, ntrain=4096, ntest=512, steps=2000, batch=256):
+    """Config 4: the warm-start network trained on cold solves of sampled
+    loads of the 2,000-bus grid and judged on held-out scenarios against
+    cold starts of the same scenarios."""
+    import numpy as np
+    import torch
+
+    from paper_2310_13143_gb300 import binding, gridgen, warmstart as ws
+
+    base = gridgen.grid_2000bus()
+    scen = gridgen.scenarios_cholesky(base, ntrain + ntest, seed=1004)
+    opts = solver_options(binding, "mixed")
+    t0 = time.perf_counter()
+    T, conv, iters, objs = ws.solve_targets(scen, opts, precision="mixed", chunk=512)
+    t_data = time.perf_counter() - t0
+    X = ws.loads_matrix(scen)
+    dims = ws.dims_for(base)
+    net = binding.Mlp(dims, max_batch=batch)
+    net.set_params(gridgen.mlp_init(dims, seed=1004))
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    net.fit_standardiser(Xd.data_ptr(), Td.data_ptr(), ntrain)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = ws.train(net, Xd, Td, ntrain, steps=steps, batch=batch, lr=1e-3, seed=1004)
+    t_train = time.perf_counter() - t0
+    test = scen[ntrain:]
+    stream = torch.cuda.Stream()
+    res = {}
+    for mode in ("cold", "warm"):
+        s = binding.Solver(test, precision="mixed")
+        s.set_stream(stream.cuda_stream)
+        s.sqp_solve_graph(opts, check_every=2)  # warm-up of the handle (graph capture)
+        pred = torch.zeros((ntest, dims[-1]), device="cuda")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        if mode == "warm":
+            net.set_stream(stream.cuda_stream)
+            net.forward(Xd[ntrain:].data_ptr(), ntest, pred.data_ptr())
+            s.set_warm_start_device(pred.data_ptr(), dims[-1], base_rho=2e4, use_rho=False)
+        s.sqp_solve_graph(opts, check_every=2)
+        b.record(stream)
+        torch.cuda.synchronize()
+        rs = [s.get_residuals(k) for k in range(ntest)]
+        ob = np.array([s.get_solution(k)["obj"] for k in range(ntest)])
+        ok = [r["result_name"] == "converged" and r["primal"] <= 1e-4 and r["dual"] <= 1e-4 for r in rs]
+        res[mode] = {"seconds": a.elapsed_time(b) / 1e3, "converged": int(sum(ok)),
+                     "admm_iters_mean": float(np.mean([r["admm_iter"] for r in rs])),
+                     "sqp_iters_mean": float(np.mean([r["sqp_iter"] for r in rs])), "obj": ob}
+        s.close()
+    net.close()
+    okc = res["cold"]["obj"]
+    rel = np.abs(res["warm"]["obj"] - okc) / np.abs(okc)
+    for m in res:
+        res[m].pop("obj")
+        res[m]["solves_per_s"] = res[m]["converged"] / res[m]["seconds"]
+    return {"train_scenarios": ntrain, "held_out": ntest, "net": dims, "train_steps": steps, "batch": batch,
+            "data_seconds": t_data, "train_seconds": t_train, "data_converged": int(conv.sum()),
+            "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-10:].mean()),
+            "cold": res["cold"], "warm": res["warm"],
+            "speedup_wall": res["cold"]["seconds"] / res["warm"]["seconds"],
+            "admm_iter_ratio": res["warm"]["admm_iters_mean"] / res["cold"]["admm_iters_mean"],
+            "objective_rel_diff_max": float(rel.max()), "objective_rel_diff_median": float(np.median(rel)),
+            "tensor_gemm": gemm_roofline()}
+
+
+def gemm_roofline(M=8192, N=8192, K=8192, reps=5):
+    """The tensor-core product alone on a large square problem: achieved
+    dense BF16 TFLOP/s against the measured cuBLAS peak."""
+    import torch
+
+    from paper_2310_13143_gb300 import binding
+
+    A = torch.randn(M, K, device="cuda").to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda").to(torch.bfloat16)
+    C = torch.empty(M, N, device="cuda", dtype=torch.float32)
+    binding.gemm_bf16(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, 1, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        binding.gemm_bf16(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, 1,
+                          torch.cuda.current_stream().cuda_stream)
+    t = (time.perf_counter() - t0) / reps
+    tf = 2.0 * M * N * K / t / 1e12
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            peak, src = float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        peak, src = 1900.0, "fallback"
+    return {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+            "traffic": None, "peak_source": src, "kernel": "k_gemm_tc", "shape": [M, N, K],
+            "timing": "host wall clock per synchronous call (includes the launch)"}
 
 
 def workload_grids(name):
@@ -392,7 +555,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--workload", default="syn2000", choices=["syn2000", "batched", "syn70k", "syn70k_x16"])
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--workload", default="syn2000", choices=["syn2000", "batched", "syn70k", "syn70k_x16", "gemm"])
+    ap.add_argument("--gemm-shape", default="8192,8192,8192")
     ap.add_argument("--sweep-iters", type=int, default=0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -406,6 +572,16 @@ def main():
         import torch
 
         torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if args.workload == "gemm":  # the tensor-core product alone (profiling and roofline studies)
+        from paper_2310_13143_gb300.build import build
+
+        build()
+        M, N, K = (int(v) for v in args.gemm_shape.split(","))
+        r = gemm_roofline(M, N, K, reps=max(args.steps, 1))
+        r.update({"metric": "BF16 tensor-core GEMM TFLOP/s", "value": r["achieved"], "unit": "TFLOP/s"})
+        if rank == 0:
+            print(json.dumps(r), flush=True)
+        return
     if args.sweep_iters > 0:  # ADMM sweep alone on a workload (profiling and roofline studies)
         from paper_2310_13143_gb300.build import build
 

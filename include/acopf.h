@@ -168,6 +168,18 @@ acopf_status sqp_solve(acopf_handle h, const sqp_options* o);
  * acopf_get_step.  The iterate itself is not changed. */
 acopf_status admm_solve_qp(acopf_handle h, double delta, const admm_options* o);
 
+/* sqp_solve with the SQP loop replayed from a CUDA graph: the first iteration
+ * runs as individual launches (its ADMM start depends on the warm start); one
+ * later iteration -- QP build, ADMM reset, the persistent sweep, step, merit
+ * test and trust-region update (Alg. 1 lines 5-14, Alg. 2) -- is captured once
+ * per handle and option set and replayed until every instance has stopped.
+ * The host reads the number of running instances from pinned memory after
+ * every check_every >= 1 replays; replays after the last instance stopped
+ * leave every instance unchanged.  Results equal those of sqp_solve.  If the
+ * handle has no stream (acopf_set_stream), an internal stream is used and the
+ * device is synchronised first.  Returns when the solve is complete. */
+acopf_status sqp_solve_graph(acopf_handle h, const sqp_options* o, int32_t check_every);
+
 /* Warm start of instance inst: x0 = NLP point in the layout of
  * acopf_set_iterate (may be NULL; pi is reset to 0), lambda0 = ADMM multipliers:
  * the lam array of acopf_admm_state (8 per branch) followed by its lg array
@@ -256,6 +268,20 @@ acopf_status acopf_get_profile_phases(acopf_handle h, double* ns);
  * fit; -1 keeps), and for the FP32 sweep the number of shared-memory
  * branch-tile buffers (1 or 2; 0 keeps). */
 acopf_status acopf_tune(acopf_handle h, int32_t block_threads, int32_t ctas_per_sm, int32_t sweep_stages);
+
+/* Autotuner of the sweep's launch shape.  If cache_path (may be NULL) names a
+ * JSON file holding an entry for this handle's key -- SM count, sweep
+ * precision and the binary orders of magnitude of the instance, bus and
+ * branch counts -- that shape is applied.  Otherwise the QP at the current
+ * iterate is built (delta 1, rho 2e4) and every shape of {64, 128, 256}
+ * threads x {as many CTAs per SM as fit, 1} x {1, 2} branch-tile buffers
+ * (FP32 sweep; FP64: 1) is timed over iters fixed ADMM iterations with CUDA
+ * events; the fastest is applied and written to the cache (other keys are
+ * kept).  shape_out (3 ints: threads, CTAs per SM, buffers) and us_per_iter
+ * (-1 when taken from the cache) may be NULL.  Resets the ADMM state: call it
+ * before setting a warm start. */
+acopf_status acopf_autotune(acopf_handle h, const char* cache_path, int32_t iters, int32_t* shape_out,
+                            double* us_per_iter);
 
 /* ---- allocation-free sweep (the paper has no counterpart) ----------------
  *

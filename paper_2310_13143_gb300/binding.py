@@ -125,6 +125,8 @@ def lib():
             "acopf_tune": (S, [H, C.c_int32, C.c_int32, C.c_int32]),
             "acopf_get_profile": (S, [H, DP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
             "acopf_set_warm_start_device": (S, [H, C.c_void_p, C.c_int64, C.c_double, S, S, S, S]),
+            "sqp_solve_graph": (S, [H, C.POINTER(sqp_options), C.c_int32]),
+            "acopf_autotune": (S, [H, C.c_char_p, C.c_int32, IP, DP]),
             "acopf_mlp_create": (S, [IP, C.c_int32, C.c_int32, C.c_int32, C.POINTER(H)]),
             "acopf_mlp_destroy": (S, [H]),
             "acopf_mlp_set_stream": (S, [H, C.c_void_p]),
@@ -155,7 +157,7 @@ EXPORTED = ["acopf_default_options", "admm_default_options", "sqp_default_option
             "acopf_set_iterate", "acopf_get_iterate", "acopf_build_qp", "acopf_get_qp", "acopf_get_admm_state",
             "acopf_set_admm_state", "admm_iterate", "acopf_get_step", "acopf_launch_count", "acopf_profile",
             "acopf_get_profile", "acopf_get_history", "admm_iterate_static", "acopf_get_profile_phases",
-            "acopf_tune", "acopf_set_warm_start_device", "acopf_mlp_create", "acopf_mlp_destroy",
+            "acopf_tune", "acopf_set_warm_start_device", "sqp_solve_graph", "acopf_autotune", "acopf_mlp_create", "acopf_mlp_destroy",
             "acopf_mlp_set_stream", "acopf_mlp_last_error", "acopf_mlp_num_params", "acopf_mlp_set_params",
             "acopf_mlp_get_params", "acopf_mlp_get_grads", "acopf_mlp_fit_standardiser",
             "acopf_mlp_get_standardiser", "acopf_mlp_forward", "acopf_mlp_train_step", "acopf_mlp_sync",
@@ -263,6 +265,17 @@ class Solver:
 
     def sqp_solve(self, opts: sqp_options | None = None):
         self._check(lib().sqp_solve(self.h, C.byref(opts or default_sqp())))
+
+    def sqp_solve_graph(self, opts: sqp_options | None = None, check_every: int = 4):
+        self._check(lib().sqp_solve_graph(self.h, C.byref(opts or default_sqp()), int(check_every)))
+
+    def autotune(self, cache_path: str | None = None, iters: int = 50):
+        """Returns ((threads, ctas_per_sm, stages), us_per_iter or -1 if cached)."""
+        shape = np.zeros(3, dtype=np.int32)
+        us = C.c_double()
+        self._check(lib().acopf_autotune(self.h, cache_path.encode() if cache_path else None, int(iters),
+                                         shape.ctypes.data_as(IP), C.byref(us)))
+        return tuple(int(v) for v in shape), us.value
 
     def admm_solve_qp(self, delta=1.0, opts: admm_options | None = None):
         self._check(lib().admm_solve_qp(self.h, float(delta), C.byref(opts or default_admm())))

@@ -81,6 +81,13 @@ static acopf_status put(Ctx* c, void* dev, const std::vector<double>& in, size_t
   return ACOPF_OK;
 }
 
+static void drop_graph(Ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->gexec = nullptr;
+  c->graph = nullptr;
+}
+
 // oracle slot s of a branch -> (end, component) of the end-major layout
 static const int kSlotEnd[8] = {0, 0, 1, 1, 0, 0, 1, 1};
 static const int kSlotComp[8] = {0, 1, 0, 1, 2, 3, 2, 3};
@@ -425,6 +432,10 @@ acopf_status acopf_destroy(acopf_handle h) {
   if (c->d.xbr) cudaFree(c->d.xbr);
   if (c->d.xgen) cudaFree(c->d.xgen);
   if (c->d.xbus) cudaFree(c->d.xbus);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  if (c->h_running) cudaFreeHost(c->h_running);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
   free(c->h_bus_off); free(c->h_br_off); free(c->h_gen_off); free(c->h_gen_perm); free(c->h_gen_iperm);
   delete c;
   return ACOPF_OK;
@@ -482,6 +493,7 @@ acopf_status acopf_tune(acopf_handle h, int32_t block_threads, int32_t ctas_per_
     if (sweep_stages > 2) return fail(c, ACOPF_EINVAL, "acopf_tune: sweep_stages must be 1 or 2");
     c->sweep_stages = sweep_stages;
   }
+  drop_graph(c);  // the launch shape is baked into a captured graph
   return ACOPF_OK;
 }
 
@@ -641,6 +653,224 @@ acopf_status sqp_solve(acopf_handle h, const sqp_options* op) {
   c->warm_x = c->warm_lam = c->warm_rho = false;
   c->qp_built = true;
   c->have_step = true;
+  return ACOPF_OK;
+}
+
+// The SQP loop with every iteration after the first replayed from one CUDA
+// graph (build, ADMM reset, the persistent sweep, step, merit, acceptance and
+// the copy of the running count to pinned host memory).  The host reads the
+// running count only every check_every replays; replays after the last
+// instance has stopped change nothing (every kernel skips stopped instances).
+acopf_status sqp_solve_graph(acopf_handle h, const sqp_options* op, int32_t check_every) {
+  Ctx* c = (Ctx*)h;
+  if (!c || check_every < 1) return fail(c, ACOPF_EINVAL, "sqp_solve_graph: bad arguments");
+  sqp_options o;
+  if (op) o = *op;
+  else sqp_default_options(&o);
+  if (o.max_sqp < 1 || !(o.delta0 > 0) || !(o.mu >= 0)) return fail(c, ACOPF_EINVAL, "sqp options out of range");
+  acopf_status s = check_admm(o.admm, c);
+  if (s) return s;
+  cudaStream_t user = c->stream;
+  if (!user) {
+    if (!c->gstream) CK(cudaStreamCreate(&c->gstream));
+    CK(cudaDeviceSynchronize());
+    c->stream = c->gstream;
+  }
+  struct Restore {
+    Ctx* c;
+    cudaStream_t s;
+    ~Restore() { c->stream = s; c->capturing = false; }
+  } restore{c, user};
+  if (!c->h_running) CK(cudaMallocHost(&c->h_running, sizeof(int)));
+  if (!c->warm_x) launch_flat_start(*c);
+  if (!c->warm_rho) launch_fill_rho(*c, o.admm.rho);
+  if ((s = reset_control(c, o, true))) return s;
+  // first iteration eagerly: its ADMM start depends on the warm start
+  launch_build(*c, false);
+  launch_admm_reset(*c, c->warm_lam ? 1 : 0);
+  if ((s = launch_sweep(*c, o.admm, 0))) return s;
+  if (o.admm.warm && o.admm.rb_period > 0) launch_commit_rho(*c);
+  launch_step(*c);
+  launch_merit(*c);
+  launch_accept_and_kkt(*c);
+  CK(cudaMemcpyAsync(c->h_running, c->d.n_running, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  if ((s = sweep_status(c))) return s;
+  int running = *c->h_running;
+  if (running > 0 && o.max_sqp > 1) {
+    if (!c->gexec || memcmp(&c->gopts, &o, sizeof(o)) != 0) {
+      drop_graph(c);
+      int64_t l0 = c->launches;
+      c->capturing = true;
+      CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      launch_build(*c, false);
+      launch_admm_reset(*c, o.admm.warm);
+      acopf_status cs = launch_sweep(*c, o.admm, 0);
+      if (o.admm.warm && o.admm.rb_period > 0) launch_commit_rho(*c);
+      launch_step(*c);
+      launch_merit(*c);
+      launch_accept_and_kkt(*c);
+      cudaMemcpyAsync(c->h_running, c->d.n_running, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+      cudaGraph_t g = nullptr;
+      cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+      c->capturing = false;
+      c->gkernels = (int)(c->launches - l0);
+      c->launches = l0;
+      if (cs) {
+        if (g) cudaGraphDestroy(g);
+        return cs;
+      }
+      CK(ce);
+      c->graph = g;
+      CK(cudaGraphInstantiate(&c->gexec, g, 0));
+      c->gopts = o;
+    }
+    for (int it = 1; it < o.max_sqp; ++it) {
+      CK(cudaGraphLaunch(c->gexec, c->stream));
+      c->launches += c->gkernels;
+      if (it % check_every == 0 || it == o.max_sqp - 1) {
+        if ((s = sweep_status(c))) return s;
+        if (*c->h_running == 0) break;
+      }
+    }
+  }
+  launch_finish(*c);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  c->warm_x = c->warm_lam = c->warm_rho = false;
+  c->qp_built = true;
+  c->have_step = true;
+  return ACOPF_OK;
+}
+
+// ----------------------------------------------------------------- autotune
+// Launch shapes of the ADMM sweep timed on the QP at the current iterate; the
+// fastest is applied and remembered in a JSON cache keyed by the GPU's SM
+// count, the sweep precision and the binary orders of magnitude of the
+// instance, bus and branch counts.
+static std::string tune_key(Ctx* c) {
+  auto lg = [](long v) {
+    int k = 0;
+    while (v > 1) { v >>= 1; ++k; }
+    return k;
+  };
+  char buf[128];
+  snprintf(buf, sizeof(buf), "sm%d-%s-K%d-B%d-L%d", c->num_sms, c->precision == ACOPF_MIXED ? "mixed" : "fp64",
+           lg(c->d.K), lg(c->d.B), lg(c->d.L));
+  return buf;
+}
+
+static std::vector<std::string> read_lines(const char* path) {
+  std::vector<std::string> out;
+  FILE* f = path ? fopen(path, "r") : nullptr;
+  if (!f) return out;
+  char line[1024];
+  while (fgets(line, sizeof(line), f)) {
+    std::string l(line);
+    while (!l.empty() && (l.back() == '\n' || l.back() == '\r')) l.pop_back();
+    out.push_back(l);
+  }
+  fclose(f);
+  return out;
+}
+
+static bool cache_lookup(const char* path, const std::string& key, int shape[3]) {
+  for (const std::string& l : read_lines(path)) {
+    if (l.find("\"key\": \"" + key + "\"") == std::string::npos) continue;
+    int bt = 0, cps = -1, st = 0;
+    const char* p = strstr(l.c_str(), "\"block_threads\":");
+    const char* q = strstr(l.c_str(), "\"ctas_per_sm\":");
+    const char* r = strstr(l.c_str(), "\"stages\":");
+    if (!p || !q || !r) continue;
+    if (sscanf(p, "\"block_threads\": %d", &bt) != 1 || sscanf(q, "\"ctas_per_sm\": %d", &cps) != 1 ||
+        sscanf(r, "\"stages\": %d", &st) != 1)
+      continue;
+    if (bt < 32 || bt > 256 || bt % 32 || cps < 0 || st < 1 || st > 2) continue;
+    shape[0] = bt; shape[1] = cps; shape[2] = st;
+    return true;
+  }
+  return false;
+}
+
+static void cache_store(const char* path, const std::string& key, const int shape[3], double us) {
+  if (!path) return;
+  std::vector<std::string> keep;
+  for (const std::string& l : read_lines(path))
+    if (l.find("\"key\":") != std::string::npos && l.find("\"key\": \"" + key + "\"") == std::string::npos) {
+      std::string e = l;
+      while (!e.empty() && (e.back() == ',' || e.back() == ' ')) e.pop_back();
+      keep.push_back(e);
+    }
+  char buf[256];
+  snprintf(buf, sizeof(buf),
+           "  {\"key\": \"%s\", \"block_threads\": %d, \"ctas_per_sm\": %d, \"stages\": %d, \"us_per_iter\": %.3f}",
+           key.c_str(), shape[0], shape[1], shape[2], us);
+  keep.push_back(buf);
+  std::string tmp = std::string(path) + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return;
+  fprintf(f, "[\n");
+  for (size_t k = 0; k < keep.size(); ++k) {
+    std::string e = keep[k];
+    size_t a = e.find('{');
+    fprintf(f, "  %s%s\n", a == std::string::npos ? e.c_str() : e.c_str() + a, k + 1 < keep.size() ? "," : "");
+  }
+  fprintf(f, "]\n");
+  fclose(f);
+  rename(tmp.c_str(), path);
+}
+
+acopf_status acopf_autotune(acopf_handle h, const char* cache_path, int32_t iters, int32_t* shape_out,
+                            double* us_per_iter) {
+  Ctx* c = (Ctx*)h;
+  if (!c || iters < 1) return fail(c, ACOPF_EINVAL, "acopf_autotune: bad arguments");
+  const std::string key = tune_key(c);
+  int best[3] = {c->block_threads, c->ctas_per_sm, c->sweep_stages};
+  double best_us = -1.0;
+  if (!cache_lookup(cache_path, key, best)) {
+    acopf_status s = acopf_build_qp(h, 1.0, 2e4, c->use_angle);
+    if (s) return s;
+    admm_options a;
+    admm_default_options(&a);
+    bool prof = c->profiling;
+    c->profiling = false;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int threads[3] = {64, 128, 256};
+    const int nst = c->precision == ACOPF_MIXED ? 2 : 1;
+    for (int ti = 0; ti < 3; ++ti)
+      for (int cps = 0; cps <= 1; ++cps)
+        for (int st = 1; st <= nst; ++st) {
+          c->block_threads = threads[ti];
+          c->ctas_per_sm = cps;
+          c->sweep_stages = st;
+          launch_admm_reset(*c, 0);
+          if ((s = launch_sweep(*c, a, iters > 4 ? iters / 4 : 1))) break;
+          CK(cudaEventRecord(e0, c->stream));
+          if ((s = launch_sweep(*c, a, iters))) break;
+          CK(cudaEventRecord(e1, c->stream));
+          if ((s = sweep_status(c))) break;
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          double us = 1e3 * ms / iters;
+          if (best_us < 0 || us < best_us) {
+            best_us = us;
+            best[0] = threads[ti]; best[1] = cps; best[2] = st;
+          }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->profiling = prof;
+    launch_admm_reset(*c, 0);
+    if (s) return s;
+    cache_store(cache_path, key, best, best_us);
+  }
+  c->block_threads = best[0];
+  c->ctas_per_sm = best[1];
+  c->sweep_stages = best[2];
+  drop_graph(c);
+  if (shape_out) { shape_out[0] = best[0]; shape_out[1] = best[1]; shape_out[2] = best[2]; }
+  if (us_per_iter) *us_per_iter = best_us;
   return ACOPF_OK;
 }
 

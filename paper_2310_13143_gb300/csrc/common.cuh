@@ -149,6 +149,14 @@ struct Ctx {
   // warm start staged by acopf_set_warm_start / acopf_set_warm_start_device
   bool warm_x = false, warm_lam = false, warm_rho = false;
   int* d_gen_iperm = nullptr;  // device copy of h_gen_iperm (allocated on first use)
+  // CUDA graph of one SQP iteration (sqp_solve_graph)
+  bool capturing = false;          // launches are being captured: no host reads, no per-sweep error reset
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  sqp_options gopts{};             // options the graph was captured with
+  int gkernels = 0;                // kernel nodes per replay
+  int* h_running = nullptr;        // pinned host copy of n_running
+  cudaStream_t gstream = nullptr;  // capture stream when the handle has none
 };
 
 // kernels, launchers (defined in the .cu files)

@@ -737,18 +737,22 @@ static acopf_status run_sweep(Ctx& c, const admm_options& o, int fixed_iters) {
   int blocks = (int)(need < maxb ? need : maxb);
   if (blocks < 1) blocks = 1;
   cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), c.stream);
-  cudaMemsetAsync(d.err, 0, sizeof(int), c.stream);
+  // inside a captured SQP iteration the error flag is not cleared: a barrier
+  // time-out stays visible to the host and makes every later sweep return at
+  // its first barrier
+  if (!c.capturing) cudaMemsetAsync(d.err, 0, sizeof(int), c.stream);
   cudaMemsetAsync(d.res_slots, 0, sizeof(unsigned long long) * 4 * d.K, c.stream);
   launch_rho_fac_reset(c);
   void* args[] = {&p};
-  if (c.profiling) cudaEventRecord(c.ev0, c.stream);
+  const bool prof = c.profiling && !c.capturing;
+  if (prof) cudaEventRecord(c.ev0, c.stream);
   cudaError_t e = cudaLaunchCooperativeKernel((void*)k_sweep<T>, dim3(blocks), dim3(threads), args, smem, c.stream);
   c.launches++;
   if (e != cudaSuccess) {
     c.last_error = std::string("sweep launch: ") + cudaGetErrorString(e);
     return ACOPF_ECUDA;
   }
-  if (c.profiling) {
+  if (prof) {
     cudaEventRecord(c.ev1, c.stream);
     cudaEventSynchronize(c.ev1);
     float ms = 0.f;

@@ -265,3 +265,44 @@ def test_mixed_sweep_many_tiles_matches_fp64():
     for key in ("x", "z", "zb"):
         a, b = out["mixed"][key], out["fp64"][key]
         np.testing.assert_allclose(a, b, rtol=0, atol=1e-3 * max(1.0, np.abs(b).max()), err_msg=key)
+
+
+def test_graph_replayed_solve_equals_eager_solve():
+    """The CUDA-graph SQP loop replays the same kernels on the same data: every
+    instance's result must equal the eager loop's, including instances that
+    stop early while others keep going."""
+    grids = [gg.grid_30bus(), gg.two_bus(), gg.geometric_grid(118, seed=11)]
+    for prec in ("fp64", "mixed"):
+        opts = binding.default_sqp(tol=1e-4, max_sqp=30, admm=dict(rho=2e4, max_iter=800, eps=1e-4,
+                                                                   eps_dual=5e-3 if prec == "mixed" else 0.0))
+        a = binding.Solver(grids, precision=prec)
+        a.sqp_solve(opts)
+        b = binding.Solver(grids, precision=prec)
+        for check in (1, 3):
+            b.sqp_solve_graph(opts, check_every=check)
+            for k in range(len(grids)):
+                ra, rb = a.get_residuals(k), b.get_residuals(k)
+                assert ra["sqp_iter"] == rb["sqp_iter"] and ra["admm_iter"] == rb["admm_iter"]
+                assert ra["result"] == rb["result"]
+                xa, _ = a.get_iterate(k)
+                xb, _ = b.get_iterate(k)
+                np.testing.assert_array_equal(xa, xb)
+        a.close()
+        b.close()
+
+
+def test_autotune_applies_and_caches_a_shape(tmp_path):
+    cache = str(tmp_path / "tune.json")
+    grids = [gg.grid_30bus()] * 4
+    s = binding.Solver(grids, precision="mixed")
+    shape, us = s.autotune(cache, iters=20)
+    assert shape[0] in (64, 128, 256) and shape[1] in (0, 1) and shape[2] in (1, 2) and us > 0
+    import json
+    entries = json.load(open(cache))
+    assert len(entries) == 1 and entries[0]["block_threads"] == shape[0]
+    shape2, us2 = s.autotune(cache, iters=20)
+    assert shape2 == shape and us2 == -1.0
+    # the tuned handle still solves correctly
+    s.sqp_solve(binding.default_sqp(tol=1e-4, admm=dict(rho=2e4, max_iter=1000, eps=1e-4, eps_dual=5e-3)))
+    assert all(s.get_residuals(k)["result_name"] == "converged" for k in range(4))
+    s.close()
