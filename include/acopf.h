@@ -104,7 +104,7 @@ typedef struct {
 } admm_options;
 
 typedef struct {
-  double mu;             /* l1 merit penalty (Sec. IV-A: 1e5) */
+  double mu;             /* l1 merit penalty (Sec. V-A: 1e5) */
   double tol;            /* primal and dual infeasibility tolerance */
   double step_tol;       /* stop when an accepted step's l_inf norm is below this */
   double delta0, delta_max, delta_min; /* trust region: initial, cap, failure threshold */

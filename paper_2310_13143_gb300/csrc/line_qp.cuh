@@ -1,6 +1,6 @@
 // The per-branch line subproblem of eq. line_kernel as a 4-variable QP,
 // solved by the augmented Lagrangian method with a projected Newton inner
-// solver (Sec. IV-A).  Host and device code: the sweep kernel calls it per
+// solver (Sec. IV-B).  Host and device code: the sweep kernel calls it per
 // branch, and the same code compiles on the host for unit checks.
 #pragma once
 

@@ -4,7 +4,7 @@
 //   phase A  one thread per generator (eq. gen_kernel, closed form) and per
 //            branch (eq. line_kernel: 4-variable QP with box, line-limit and
 //            angle rows, solved by an augmented Lagrangian whose subproblems
-//            are solved by projected Newton -- Sec. IV-A);
+//            are solved by projected Newton -- Sec. IV-B);
 //   barrier
 //   phase B  one thread per bus (eq. bus_kernel, closed form from the 2x2
 //            system of the power-balance rows), fused with the multiplier
