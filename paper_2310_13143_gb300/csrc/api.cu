@@ -323,6 +323,43 @@ acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_o
     end_idx[end_ptr[f[l]] + fill[f[l]]++] = 2 * l;
     end_idx[end_ptr[t[l]] + fill[t[l]]++] = 2 * l + 1;
   }
+  // bus update work list and its warp tasks (consecutive whole buses, at most
+  // 32 entries per task; a bus with more entries is a task of its own)
+  const size_t E = (size_t)G + 2 * (size_t)L;
+  std::vector<int> ent(E), ebus(E), pent, pbus, pinst, big;
+  {
+    size_t q = 0;
+    for (int i = 0; i < B; ++i) {
+      for (int g = gen_ptr[i]; g < gen_ptr[i + 1]; ++g) { ent[q] = -(g + 1); ebus[q++] = i; }
+      for (int e2 = end_ptr[i]; e2 < end_ptr[i + 1]; ++e2) { ent[q] = end_idx[e2]; ebus[q++] = i; }
+    }
+    size_t q0 = 0;   // first entry of the open task
+    size_t cnt = 0;  // its entries
+    auto close = [&]() {
+      if (cnt == 0) return;
+      for (size_t j = 0; j < 32; ++j) {
+        bool in = j < cnt;
+        pent.push_back(in ? ent[q0 + j] : 0);
+        pbus.push_back(in ? ebus[q0 + j] : -1);
+        pinst.push_back(in ? bus_inst[ebus[q0 + j]] : -1);
+      }
+      q0 += cnt;
+      cnt = 0;
+    };
+    for (int i = 0; i < B; ++i) {
+      size_t n = (size_t)(gen_ptr[i + 1] - gen_ptr[i]) + (size_t)(end_ptr[i + 1] - end_ptr[i]);
+      if (n > 32) {
+        close();
+        big.push_back((int)q0);
+        big.push_back((int)(q0 + n));
+        q0 += n;
+        continue;
+      }
+      if (cnt + n > 32) close();
+      cnt += n;
+    }
+    close();
+  }
 
   // ---- device allocation
   Dev& d = c->d;
@@ -334,6 +371,11 @@ acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_o
   A(d.bus_inst, B); A(d.br_inst, L); A(d.gen_inst, G);
   A(d.pd, B); A(d.qd, B); A(d.gs, B); A(d.bs, B); A(d.wmin, B); A(d.wmax, B); A(d.isref, B);
   A(d.end_ptr, B + 1); A(d.end_idx, 2 * (size_t)L); A(d.gen_ptr, B + 1);
+  A(d.ent, E); A(d.ebus, E); A(d.pent, pent.size()); A(d.pbus, pbus.size()); A(d.pinst, pinst.size());
+  A(d.big, big.size());
+  d.E = (int)E;
+  d.NT = (int)(pbus.size() / 32);
+  d.NBIG = (int)(big.size() / 2);
   A(d.f, L); A(d.t, L); A(d.Y, 8 * (size_t)L); A(d.s2, L); A(d.angmin, L); A(d.angmax, L);
   A(d.gbus, G); A(d.pmin, G); A(d.pmax, G); A(d.qmin, G); A(d.qmax, G); A(d.cq, G); A(d.cl, G); A(d.cc, G);
   A(d.pg, G); A(d.qg, G); A(d.w, B); A(d.th, B); A(d.wr, L); A(d.wi, L); A(d.pi, 4 * (size_t)L);
@@ -372,6 +414,7 @@ acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_o
   U(d.bus_inst, bus_inst); U(d.br_inst, br_inst); U(d.gen_inst, gen_inst_s);
   U(d.pd, pd); U(d.qd, qd); U(d.gs, gs); U(d.bs, bs); U(d.wmin, wmin); U(d.wmax, wmax); U(d.isref, isref);
   U(d.end_ptr, end_ptr); U(d.end_idx, end_idx); U(d.gen_ptr, gen_ptr);
+  U(d.ent, ent); U(d.ebus, ebus); U(d.pent, pent); U(d.pbus, pbus); U(d.pinst, pinst); U(d.big, big);
   U(d.f, f); U(d.t, t); U(d.s2, s2); U(d.angmin, amin); U(d.angmax, amax);
   U(d.gbus, gbus);
   std::vector<double> v_pmin = P(pmin), v_pmax = P(pmax), v_qmin = P(qmin), v_qmax = P(qmax), v_cq = P(cq),

@@ -65,6 +65,16 @@ struct Dev {
   double *pd, *qd, *gs, *bs, *wmin, *wmax;
   int* isref;
   int *end_ptr, *end_idx, *gen_ptr;
+  // bus update work list: entry q (bus order: the bus's generators, then its
+  // branch ends) is ent[q] = -(g + 1) for generator g or the end id 2 l + side,
+  // ebus[q] its bus.  Warp tasks of consecutive whole buses with at most 32
+  // entries are stored padded: slot 32 t + j holds lane j's entry (pent), bus
+  // (pbus, -1: empty) and instance (pinst).  A bus with more than 32 entries
+  // is a big task: entries [big[2 b], big[2 b + 1]) of ent/ebus.
+  int *ent, *ebus;
+  int *pent, *pbus, *pinst;
+  int* big;
+  int E, NT, NBIG;
   // branches
   int *f, *t;
   double* Y;        // [8][L]: gii bii gij bij gji bji gjj bjj
@@ -138,14 +148,14 @@ struct Ctx {
   int* h_gen_off = nullptr;
   int* h_gen_perm = nullptr;   // internal index -> user index (global)
   int* h_gen_iperm = nullptr;  // user index -> internal index
-  void* allocs[128];
+  void* allocs[192];
   int nallocs = 0;
   // sweep timing (acopf_profile)
   bool profiling = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double prof_ms = 0.0;
   int64_t prof_sweeps = 0, prof_iters = 0;
-  int sweep_stages = 2;  // FP32 sweep: branch-tile buffers per CTA (1 or 2)
+  int sweep_stages = 1;  // FP32 sweep: branch-tile buffers per CTA (1 or 2)
   // warm start staged by acopf_set_warm_start / acopf_set_warm_start_device
   bool warm_x = false, warm_lam = false, warm_rho = false;
   int* d_gen_iperm = nullptr;  // device copy of h_gen_iperm (allocated on first use)

@@ -6,11 +6,13 @@
 //            angle rows, solved by an augmented Lagrangian whose subproblems
 //            are solved by projected Newton -- Sec. IV-B);
 //   barrier
-//   phase B  one thread per bus (eq. bus_kernel, closed form from the 2x2
-//            system of the power-balance rows), fused with the multiplier
-//            update of every coupling owned by the bus (eq. multiplier) and
-//            the primal/dual residuals r = x - z, s = rho (z+ - z) (Sec. IV-B),
-//            reduced with warp shuffles and one 64-bit atomicMax per warp;
+//   phase B  one lane per generator or branch end, one warp per task of
+//            consecutive buses (eq. bus_kernel, closed form from the 2x2
+//            system of the power-balance rows, per-bus sums by a segmented
+//            warp scan), fused with the multiplier update of every coupling
+//            (eq. multiplier) and the primal/dual residuals r = x - z,
+//            s = rho (z+ - z) (Sec. IV-B), reduced with warp shuffles and one
+//            64-bit atomicMax per run of lanes of one instance;
 //   barrier
 //   every CTA reads the per-instance residual slots and decides, identically,
 //   which instances have converged; finished instances are skipped.
@@ -301,170 +303,225 @@ __device__ __forceinline__ void res_max2(unsigned long long* slots, int K, int s
   }
 }
 
+// ---------------------------------------------------------- bus update
+// Bus update (eq. bus_kernel), multiplier update (eq. multiplier) and
+// residuals, one warp per task of consecutive whole buses: lane j takes one
+// entry -- a generator or a branch end -- of the task's buses and loads its
+// couplings; the per-bus sums of the 2x2 system are formed by a segmented
+// warp scan over the bus ids (a bus's entries are consecutive lanes); the
+// segment's last lane solves its bus and the solution is broadcast back to
+// the segment, where every lane updates its own coupling.
+
+struct Slot {
+  int bus, code, inst;  // bus -1: empty lane
+};
+
+__device__ __forceinline__ Slot load_slot(const Dev& d, int t, int lane) {
+  const size_t i = 32 * (size_t)t + lane;
+  Slot s;
+  s.bus = d.pbus[i];
+  s.code = d.pent[i];
+  s.inst = d.pinst[i];
+  return s;
+}
+
 template <typename T>
-__device__ __forceinline__ void bus_phase(const SweepP<T>& p, int i, bool check, int slot, T& rmax,
-                                          T& smax) {
-  (void)slot;
-  const Dev& d = p.d;
-  V4<T> br = ((const V4<T>*)d.brec)[i];  // pdk qdk gs bs
-  const V4<T>* X = (const V4<T>*)d.X;
-  V4<T>* Z = (V4<T>*)d.Z;
-  V4<T>* LM = (V4<T>*)d.LAM;
-  const V2<T>* XG = (const V2<T>*)d.XG;
-  V2<T>* ZG = (V2<T>*)d.ZG;
-  V2<T>* LG = (V2<T>*)d.LG;
-  const V4<T>* GR = (const V4<T>*)d.grec;
-  const T* rl = (const T*)d.trho_l;
-  int g0 = d.gen_ptr[i], g1 = d.gen_ptr[i + 1];
-  int e0 = d.end_ptr[i], e1 = d.end_ptr[i + 1];
-  // The first ME branch ends and MG generators of the bus are loaded in one
-  // batch and kept in registers for both passes (a bus has 2.7 ends on
-  // average); any further ones are streamed by the remainder loops.
-  constexpr int ME = sizeof(T) == 4 ? 4 : 2, MG = sizeof(T) == 4 ? 2 : 1;
-  const int ne = e1 - e0, ng = g1 - g0;
-  int lid[ME];
-  V4<T> xe[ME], lme[ME], zoe[ME];
-  T re[ME];
-  V2<T> xgc[MG], lgc[MG], zgc[MG];
-  T rgc[MG];
-#pragma unroll
-  for (int k = 0; k < ME; ++k) lid[k] = k < ne ? d.end_idx[e0 + k] : 0;
-#pragma unroll
-  for (int k = 0; k < ME; ++k)
-    if (k < ne) {
-      xe[k] = X[lid[k]];
-      lme[k] = LM[lid[k]];
-      zoe[k] = Z[lid[k]];
-      re[k] = rl[lid[k] >> 1];
-    }
-#pragma unroll
-  for (int k = 0; k < MG; ++k)
-    if (k < ng) {
-      xgc[k] = XG[g0 + k];
-      lgc[k] = LG[g0 + k];
-      zgc[k] = ZG[g0 + k];
-      rgc[k] = GR[d.G + g0 + k].z;
-    }
-  // pass 1: the 2x2 system (AQ^-1A') lambda = AQ^-1 c - b, c = lambda + rho x
-  T M11 = 0, M22 = 0, v1 = 0, v2 = 0, Qw = 0, cw = 0, Qt = 0, ct = 0;
-  for (int k = 0; k < ng; ++k) {
-    V2<T> x, lm;
-    T r;
-    if (k < MG) {
-#pragma unroll
-      for (int q = 0; q < MG; ++q)
-        if (q == k) { x = xgc[q]; lm = lgc[q]; r = rgc[q]; }
-    } else {
-      x = XG[g0 + k]; lm = LG[g0 + k]; r = GR[d.G + g0 + k].z;
-    }
-    M11 += T(1) / r;
-    M22 += T(1) / r;
-    v1 += (lm.x + r * x.x) / r;
-    v2 += (lm.y + r * x.y) / r;
+__device__ __forceinline__ void entry_load(const Dev& d, int c, V4<T>& x, V4<T>& lm, V4<T>& zo, T& r) {
+  if (c < 0) {
+    const int g = -c - 1;
+    V2<T> a = ((const V2<T>*)d.XG)[g], b = ((const V2<T>*)d.LG)[g], z = ((const V2<T>*)d.ZG)[g];
+    r = ((const V4<T>*)d.grec)[d.G + g].z;
+    x = {a.x, a.y, T(0), T(0)};
+    lm = {b.x, b.y, T(0), T(0)};
+    zo = {z.x, z.y, T(0), T(0)};
+  } else {
+    x = ((const V4<T>*)d.X)[c];
+    lm = ((const V4<T>*)d.LAM)[c];
+    zo = ((const V4<T>*)d.Z)[c];
+    r = ((const T*)d.trho_l)[c >> 1];
   }
-  for (int k = 0; k < ne; ++k) {
-    V4<T> x, lm;
-    T r;
-    if (k < ME) {
-#pragma unroll
-      for (int q = 0; q < ME; ++q)
-        if (q == k) { x = xe[q]; lm = lme[q]; r = re[q]; }
-    } else {
-      int le = d.end_idx[e0 + k];
-      x = X[le]; lm = LM[le]; r = rl[le >> 1];
-    }
-    M11 += T(1) / r;
-    M22 += T(1) / r;
-    v1 -= (lm.x + r * x.x) / r;
-    v2 -= (lm.y + r * x.y) / r;
-    Qw += r;
-    cw += lm.z + r * x.z;
-    Qt += r;
-    ct += lm.w + r * x.w;
+}
+
+// contributions to the bus sums: c = lambda + rho x per coupling; the 2x2
+// matrix sums 1/rho over every coupled flow, generators enter with +, branch
+// ends with - (they draw power from the bus)
+template <typename T>
+__device__ __forceinline__ void entry_sums(int c, const V4<T>& x, const V4<T>& lm, T r, T* S) {
+  S[0] += T(1) / r;
+  if (c < 0) {
+    S[1] += (lm.x + r * x.x) / r;
+    S[2] += (lm.y + r * x.y) / r;
+  } else {
+    S[1] -= (lm.x + r * x.x) / r;
+    S[2] -= (lm.y + r * x.y) / r;
+    S[3] += r;
+    S[4] += lm.z + r * x.z;
+    S[5] += lm.w + r * x.w;
   }
-  T gsh = br.z, bsh = br.w;
-  T iQw = Qw > T(0) ? T(1) / Qw : T(0);  // a bus without branch ends has no voltage copies
-  M11 += gsh * gsh * iQw;
-  M22 += bsh * bsh * iQw;
-  T M12 = -gsh * bsh * iQw;
-  v1 += -gsh * cw * iQw - br.x;
-  v2 += bsh * cw * iQw - br.y;
-  T det = M11 * M22 - M12 * M12;
-  T n1 = (M22 * v1 - M12 * v2) / det;
-  T n2 = (M11 * v2 - M12 * v1) / det;
-  T dw = (cw + gsh * n1 - bsh * n2) * iQw;
-  T dth = (d.isref[i] || !(Qt > T(0))) ? T(0) : ct / Qt;
-  // pass 2: bus-side values, multiplier update (eq. multiplier), residuals
-  T rm = T(0), sm = T(0);
-  for (int k = 0; k < ng; ++k) {
-    V2<T> x, lm, zo;
-    T r;
-    if (k < MG) {
-#pragma unroll
-      for (int q = 0; q < MG; ++q)
-        if (q == k) { x = xgc[q]; lm = lgc[q]; zo = zgc[q]; r = rgc[q]; }
-    } else {
-      x = XG[g0 + k]; lm = LG[g0 + k]; zo = ZG[g0 + k]; r = GR[d.G + g0 + k].z;
-    }
+}
+
+// the 2x2 system (A Q^-1 A') nu = A Q^-1 c - b of the bus's power-balance rows
+// with shunts, then d_w and d_theta; writes ZB, NU
+template <typename T>
+__device__ __forceinline__ void bus_solve(const Dev& d, int bus, V4<T> br, int isref, const T* S, T& n1, T& n2,
+                                          T& dw, T& dth) {
+  const T gsh = br.z, bsh = br.w;
+  const T iQw = S[3] > T(0) ? T(1) / S[3] : T(0);  // a bus without branch ends has no voltage copies
+  const T M11 = S[0] + gsh * gsh * iQw;
+  const T M22 = S[0] + bsh * bsh * iQw;
+  const T M12 = -gsh * bsh * iQw;
+  const T v1 = S[1] - gsh * S[4] * iQw - br.x;
+  const T v2 = S[2] + bsh * S[4] * iQw - br.y;
+  const T det = M11 * M22 - M12 * M12;
+  n1 = (M22 * v1 - M12 * v2) / det;
+  n2 = (M11 * v2 - M12 * v1) / det;
+  dw = (S[4] + gsh * n1 - bsh * n2) * iQw;
+  dth = (isref || !(S[3] > T(0))) ? T(0) : S[5] / S[3];
+  V2<T> zb, nu;
+  zb.x = dw; zb.y = dth;
+  nu.x = n1; nu.y = n2;
+  ((V2<T>*)d.ZB)[bus] = zb;
+  ((V2<T>*)d.NU)[bus] = nu;
+}
+
+// bus-side value, multiplier update and residuals of one coupling
+template <typename T>
+__device__ __forceinline__ void entry_update(const Dev& d, int c, const V4<T>& x, const V4<T>& lm, const V4<T>& zo, T r,
+                                             T n1, T n2, T dw, T dth, T& rm, T& sm) {
+  if (c < 0) {
+    const int g = -c - 1;
     V2<T> zn, ln;
     zn.x = (lm.x + r * x.x - n1) / r;
     zn.y = (lm.y + r * x.y - n2) / r;
-    if (check) {
-      sm = fmax(sm, fabs(r * (zn.x - zo.x)));
-      sm = fmax(sm, fabs(r * (zn.y - zo.y)));
-    }
-    T rx = x.x - zn.x, ry = x.y - zn.y;
+    sm = fmax(sm, r * fmax(fabs(zn.x - zo.x), fabs(zn.y - zo.y)));
+    const T rx = x.x - zn.x, ry = x.y - zn.y;
     rm = fmax(rm, fmax(fabs(rx), fabs(ry)));
     ln.x = lm.x + r * rx;
     ln.y = lm.y + r * ry;
-    ZG[g0 + k] = zn;
-    LG[g0 + k] = ln;
-  }
-  for (int k = 0; k < ne; ++k) {
-    V4<T> x, lm, zo;
-    T r;
-    int le;
-    if (k < ME) {
-#pragma unroll
-      for (int q = 0; q < ME; ++q)
-        if (q == k) { x = xe[q]; lm = lme[q]; zo = zoe[q]; r = re[q]; le = lid[q]; }
-    } else {
-      le = d.end_idx[e0 + k];
-      x = X[le]; lm = LM[le]; zo = Z[le]; r = rl[le >> 1];
-    }
+    ((V2<T>*)d.ZG)[g] = zn;
+    ((V2<T>*)d.LG)[g] = ln;
+  } else {
     V4<T> zn, ln;
     zn.x = (lm.x + r * x.x + n1) / r;
     zn.y = (lm.y + r * x.y + n2) / r;
     zn.z = dw;
     zn.w = dth;
-    if (check) {
-      T s1 = fmax(fabs(zn.x - zo.x), fabs(zn.y - zo.y));
-      T s2 = fmax(fabs(zn.z - zo.z), fabs(zn.w - zo.w));
-      sm = fmax(sm, r * fmax(s1, s2));
-    }
-    T rx = x.x - zn.x, ry = x.y - zn.y, rw = x.z - zn.z, rt = x.w - zn.w;
+    const T a1 = fmax(fabs(zn.x - zo.x), fabs(zn.y - zo.y));
+    const T a2 = fmax(fabs(zn.z - zo.z), fabs(zn.w - zo.w));
+    sm = fmax(sm, r * fmax(a1, a2));
+    const T rx = x.x - zn.x, ry = x.y - zn.y, rw = x.z - zn.z, rt = x.w - zn.w;
     rm = fmax(rm, fmax(fmax(fabs(rx), fabs(ry)), fmax(fabs(rw), fabs(rt))));
     ln.x = lm.x + r * rx;
     ln.y = lm.y + r * ry;
     ln.z = lm.z + r * rw;
     ln.w = lm.w + r * rt;
-    Z[le] = zn;
-    LM[le] = ln;
+    ((V4<T>*)d.Z)[c] = zn;
+    ((V4<T>*)d.LAM)[c] = ln;
   }
-  V2<T> zb, nu;
-  zb.x = dw; zb.y = dth;
-  nu.x = n1; nu.y = n2;
-  ((V2<T>*)d.ZB)[i] = zb;
-  ((V2<T>*)d.NU)[i] = nu;
-  // a NaN must not pass the residual test
+}
+
+// segmented inclusive scan of the six sums by bus id: the last lane of each
+// run of equal ids ends with its bus's totals
+template <typename T>
+__device__ __forceinline__ void seg_scan(int bus, T* S) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T a[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a[k] = __shfl_up_sync(FULL, S[k], o);
+    const int bu = __shfl_up_sync(FULL, bus, o);
+    if (lane >= o && bu == bus) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) S[k] += a[k];
+    }
+  }
+}
+
+// one task of at most 32 entries; all 32 lanes call it
+template <typename T>
+__device__ __forceinline__ void bus_task(const SweepP<T>& p, Slot s, int slot, const int* s_done) {
+  const Dev& d = p.d;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int bus = s.bus, inst = s.inst;
+  if (bus >= 0 && s_done[inst]) bus = inst = -1;
+  const int bnext = __shfl_down_sync(FULL, bus, 1);
+  const bool last = bus >= 0 && (lane == 31 || bnext != bus);
+  V4<T> x = {0, 0, 0, 0}, lm = {0, 0, 0, 0}, zo = {0, 0, 0, 0};
+  T r = T(1);
+  V4<T> br = {0, 0, 0, 0};
+  int isref = 0;
+  // every load of the task is issued here, before any is used
+  if (bus >= 0) entry_load(d, s.code, x, lm, zo, r);
+  if (last) {
+    br = ((const V4<T>*)d.brec)[bus];  // pdk qdk gs bs
+    isref = d.isref[bus];
+  }
+  T S[6] = {0, 0, 0, 0, 0, 0};
+  if (bus >= 0) entry_sums(s.code, x, lm, r, S);
+  seg_scan(bus, S);
+  T n1 = 0, n2 = 0, dw = 0, dth = 0;
+  if (last) bus_solve(d, bus, br, isref, S, n1, n2, dw, dth);
+  const unsigned after = __ballot_sync(FULL, last) >> lane;
+  const int src = after ? lane + __ffs(after) - 1 : lane;
+  n1 = __shfl_sync(FULL, n1, src);
+  n2 = __shfl_sync(FULL, n2, src);
+  dw = __shfl_sync(FULL, dw, src);
+  dth = __shfl_sync(FULL, dth, src);
+  T rm = T(0), sm = T(0);
+  if (bus >= 0) {
+    entry_update(d, s.code, x, lm, zo, r, n1, n2, dw, dth, rm, sm);
+    // a NaN must not pass the residual test
+    if (!(rm == rm)) rm = T(1e30);
+    if (!(sm == sm)) sm = T(1e30);
+  }
+  res_max2(d.res_slots, d.K, slot, rm, sm, inst);
+}
+
+// one bus with more than 32 entries (entries [q0, q1) of ent); lanes loop
+template <typename T>
+__device__ void bus_task_big(const SweepP<T>& p, int q0, int q1, int slot, const int* s_done) {
+  const Dev& d = p.d;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int bus = d.ebus[q0];
+  const int inst = d.bus_inst[bus];
+  if (s_done[inst]) {
+    res_max2(d.res_slots, d.K, slot, T(0), T(0), -1);
+    return;
+  }
+  T S[6] = {0, 0, 0, 0, 0, 0};
+  for (int q = q0 + lane; q < q1; q += 32) {
+    V4<T> x, lm, zo;
+    T r;
+    const int c = d.ent[q];
+    entry_load(d, c, x, lm, zo, r);
+    entry_sums(c, x, lm, r, S);
+  }
+  seg_scan(bus, S);
+  T n1 = 0, n2 = 0, dw = 0, dth = 0;
+  if (lane == 31) bus_solve(d, bus, ((const V4<T>*)d.brec)[bus], d.isref[bus], S, n1, n2, dw, dth);
+  n1 = __shfl_sync(FULL, n1, 31);
+  n2 = __shfl_sync(FULL, n2, 31);
+  dw = __shfl_sync(FULL, dw, 31);
+  dth = __shfl_sync(FULL, dth, 31);
+  T rm = T(0), sm = T(0);
+  for (int q = q0 + lane; q < q1; q += 32) {
+    V4<T> x, lm, zo;
+    T r;
+    const int c = d.ent[q];
+    entry_load(d, c, x, lm, zo, r);
+    entry_update(d, c, x, lm, zo, r, n1, n2, dw, dth, rm, sm);
+  }
   if (!(rm == rm)) rm = T(1e30);
   if (!(sm == sm)) sm = T(1e30);
-  rmax = rm;
-  smax = sm;
+  res_max2(d.res_slots, d.K, slot, rm, sm, inst);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_sweep(SweepP<T> p) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sweep(SweepP<T> p) {
   const Dev& d = p.d;
   extern __shared__ __align__(128) int s_done[];  // finished flags (K ints), penalty factors (K floats), tiles
   const int K = d.K;
@@ -573,17 +630,19 @@ __global__ void __launch_bounds__(256) k_sweep(SweepP<T> p) {
     if (prof) { tp1 = gtimer(); atomicAdd(&d.phase_ns[0], tp1 - tp0); }
     if (!grid_barrier(d.bar, d.err, p.spin_limit)) { aborted = true; break; }
     if (prof) { tp0 = gtimer(); atomicAdd(&d.phase_ns[1], tp0 - tp1); }
-    // phase B: buses; the loop bound is uniform per warp so that all lanes reduce together
-    for (int i0 = tid - (threadIdx.x & 31); i0 < d.B; i0 += nthreads) {
-      int i = i0 + (threadIdx.x & 31);
-      int k = -1;
-      T rm = T(0), sm = T(0);
-      if (i < d.B) {
-        k = d.bus_inst[i];
-        if (s_done[k]) k = -1;
-        else bus_phase(p, i, true, slot, rm, sm);
+    // phase B: buses, one warp task (consecutive whole buses) at a time, the
+    // next task's slots loaded while the current one is solved; loop bounds
+    // are uniform per warp so that all lanes reduce together
+    {
+      const int lane = threadIdx.x & 31, wid = tid >> 5, nw = nthreads >> 5;
+      Slot nxt = {-1, 0, -1};
+      if (wid < d.NT) nxt = load_slot(d, wid, lane);
+      for (int t = wid; t < d.NT; t += nw) {
+        const Slot cur = nxt;
+        if (t + nw < d.NT) nxt = load_slot(d, t + nw, lane);
+        bus_task(p, cur, slot, s_done);
       }
-      res_max2(d.res_slots, K, slot, rm, sm, k);
+      for (int b = wid; b < d.NBIG; b += nw) bus_task_big(p, d.big[2 * b], d.big[2 * b + 1], slot, s_done);
     }
     if (prof) { tp1 = gtimer(); atomicAdd(&d.phase_ns[2], tp1 - tp0); }
     if (!grid_barrier(d.bar, d.err, p.spin_limit)) { aborted = true; break; }

@@ -447,6 +447,16 @@ def scenarios_rff(grid: Grid, n: int, seed: int, sigma: float = 0.05, ell: float
 # --------------------------------------------------------------------------
 # named workloads
 # --------------------------------------------------------------------------
+def hub_grid(nspokes: int = 40, seed: int = 21) -> Grid:
+    """One hub bus joined to nspokes spoke buses, the spokes joined in a ring:
+    the hub has nspokes incident branches (a bus of unusually high degree)."""
+    rng = np.random.default_rng(seed)
+    n = nspokes + 1
+    edges = [(0, k) for k in range(1, n)] + [(k, k % nspokes + 1) for k in range(1, n)]
+    return _assemble(n, edges, max(2, n // 5), int(0.6 * n), rng, xy=rng.random((n, 2)), name=f"hub{n}-s{seed}",
+                     spread=False)
+
+
 def grid_30bus(seed: int = 3) -> Grid:
     """30 buses, 41 branches (a 29-edge spanning tree plus 12 extra edges),
     6 generators, 20 loads."""

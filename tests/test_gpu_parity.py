@@ -45,6 +45,7 @@ GRIDS = {
     "syn30_nolimits": lambda: _with(gg.grid_30bus(), rate=np.zeros(41), angmin=np.full(41, -7.0),
                                     angmax=np.full(41, 7.0)),
     "syn118": lambda: gg.geometric_grid(118, seed=7),
+    "hub41": lambda: gg.hub_grid(40),  # a bus with 40 branch ends (more than one warp task)
 }
 
 
@@ -95,7 +96,7 @@ def _gpu_state_from(st):
             "zb": st["zb"], "nu": st["nu"], "ul": st["ul"]}
 
 
-@pytest.mark.parametrize("name", ["syn30", "syn30_shunt_tap", "syn118", "two_bus"])
+@pytest.mark.parametrize("name", ["syn30", "syn30_shunt_tap", "syn118", "two_bus", "hub41"])
 @pytest.mark.parametrize("iters", [1, 3])
 def test_admm_iterations_match_oracle(name, iters):
     g = GRIDS[name]()
@@ -226,7 +227,7 @@ def test_residual_balancing_matches_oracle():
         np.testing.assert_allclose(a, b, rtol=0, atol=1e-7 * max(1.0, np.abs(b).max()), err_msg=gk)
 
 
-@pytest.mark.parametrize("name", ["syn30", "syn118", "syn30_shunt_tap"])
+@pytest.mark.parametrize("name", ["syn30", "syn118", "syn30_shunt_tap", "hub41"])
 @pytest.mark.parametrize("iters", [1, 3])
 def test_admm_iterations_mixed_precision(name, iters):
     """FP32 sweep (branch tiles staged in shared memory by bulk copies) against
