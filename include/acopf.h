@@ -265,8 +265,9 @@ acopf_status acopf_get_profile_phases(acopf_handle h, double* ns);
 
 /* Launch shape of the ADMM sweep (the autotuner's knobs): threads per CTA
  * (32..256, multiple of 32; 0 keeps), resident CTAs per SM (0 = as many as
- * fit; -1 keeps), and for the FP32 sweep the number of shared-memory
- * branch-tile buffers (1 or 2; 0 keeps). */
+ * fit; -1 keeps), and for the FP32 sweep how branch records reach the line
+ * solves: 1 or 2 shared-memory tile buffers filled by bulk async copies, or 0
+ * = read in place from global memory (-1 keeps). */
 acopf_status acopf_tune(acopf_handle h, int32_t block_threads, int32_t ctas_per_sm, int32_t sweep_stages);
 
 /* Autotuner of the sweep's launch shape.  If cache_path (may be NULL) names a
@@ -274,8 +275,8 @@ acopf_status acopf_tune(acopf_handle h, int32_t block_threads, int32_t ctas_per_
  * precision and the binary orders of magnitude of the instance, bus and
  * branch counts -- that shape is applied.  Otherwise the QP at the current
  * iterate is built (delta 1, rho 2e4) and every shape of {64, 128, 256}
- * threads x {as many CTAs per SM as fit, 1} x {1, 2} branch-tile buffers
- * (FP32 sweep; FP64: 1) is timed over iters fixed ADMM iterations with CUDA
+ * threads x {as many CTAs per SM as fit, 1} x {0, 1, 2} branch-tile buffers
+ * (FP32 sweep; FP64: 0) is timed over iters fixed ADMM iterations with CUDA
  * events; the fastest is applied and written to the cache (other keys are
  * kept).  shape_out (3 ints: threads, CTAs per SM, buffers) and us_per_iter
  * (-1 when taken from the cache) may be NULL.  Resets the ADMM state: call it

@@ -389,7 +389,7 @@ class Solver:
         self._check(lib().acopf_get_profile_phases(self.h, _dp(ns)))
         return dict(phase_a_ns=ns[0], wait1_ns=ns[1], phase_b_ns=ns[2], wait2_ns=ns[3])
 
-    def tune(self, block_threads=0, ctas_per_sm=-1, sweep_stages=0):
+    def tune(self, block_threads=0, ctas_per_sm=-1, sweep_stages=-1):
         self._check(lib().acopf_tune(self.h, block_threads, ctas_per_sm, sweep_stages))
 
     def launch_count(self):

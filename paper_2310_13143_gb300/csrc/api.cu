@@ -532,8 +532,8 @@ acopf_status acopf_tune(acopf_handle h, int32_t block_threads, int32_t ctas_per_
     c->block_threads = block_threads;
   }
   if (ctas_per_sm >= 0) c->ctas_per_sm = ctas_per_sm;
-  if (sweep_stages > 0) {
-    if (sweep_stages > 2) return fail(c, ACOPF_EINVAL, "acopf_tune: sweep_stages must be 1 or 2");
+  if (sweep_stages >= 0) {
+    if (sweep_stages > 2) return fail(c, ACOPF_EINVAL, "acopf_tune: sweep_stages must be 0, 1 or 2");
     c->sweep_stages = sweep_stages;
   }
   drop_graph(c);  // the launch shape is baked into a captured graph
@@ -827,7 +827,7 @@ static bool cache_lookup(const char* path, const std::string& key, int shape[3])
     if (sscanf(p, "\"block_threads\": %d", &bt) != 1 || sscanf(q, "\"ctas_per_sm\": %d", &cps) != 1 ||
         sscanf(r, "\"stages\": %d", &st) != 1)
       continue;
-    if (bt < 32 || bt > 256 || bt % 32 || cps < 0 || st < 1 || st > 2) continue;
+    if (bt < 32 || bt > 256 || bt % 32 || cps < 0 || st < 0 || st > 2) continue;
     shape[0] = bt; shape[1] = cps; shape[2] = st;
     return true;
   }
@@ -880,10 +880,10 @@ acopf_status acopf_autotune(acopf_handle h, const char* cache_path, int32_t iter
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     const int threads[3] = {64, 128, 256};
-    const int nst = c->precision == ACOPF_MIXED ? 2 : 1;
+    const int nst = c->precision == ACOPF_MIXED ? 2 : 0;
     for (int ti = 0; ti < 3; ++ti)
       for (int cps = 0; cps <= 1; ++cps)
-        for (int st = 1; st <= nst; ++st) {
+        for (int st = 0; st <= nst; ++st) {
           c->block_threads = threads[ti];
           c->ctas_per_sm = cps;
           c->sweep_stages = st;

@@ -155,7 +155,7 @@ struct Ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double prof_ms = 0.0;
   int64_t prof_sweeps = 0, prof_iters = 0;
-  int sweep_stages = 1;  // FP32 sweep: branch-tile buffers per CTA (1 or 2)
+  int sweep_stages = 0;  // FP32 sweep: branch-tile buffers per CTA (0: records read in place)
   // warm start staged by acopf_set_warm_start / acopf_set_warm_start_device
   bool warm_x = false, warm_lam = false, warm_rho = false;
   int* d_gen_iperm = nullptr;  // device copy of h_gen_iperm (allocated on first use)

@@ -42,7 +42,7 @@ struct SweepP {
   long long spin_limit;
   int rb_period;
   double rb_mu, rb_tau;
-  int stages;     // FP32 sweep: 1 or 2 branch-tile buffers
+  int stages;     // FP32 sweep: 0 (branches read their records from global memory), 1 or 2 branch-tile buffers
   int profile;    // accumulate CTA 0's phase times into d.phase_ns
 };
 
@@ -528,8 +528,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sweep(SweepP<T>
   float* s_scale = (float*)(s_done + K);
   const int nthreads = gridDim.x * blockDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  // FP32 sweep: branch tiles of blockDim.x are staged in two shared-memory buffers
-  constexpr bool kTiled = sizeof(T) == 4;
+  // FP32 sweep: branch tiles of blockDim.x are staged in one or two
+  // shared-memory buffers (stages 1, 2), or read from global memory (stages 0)
+  const bool kTiled = sizeof(T) == 4 && p.stages > 0;
   const int tile = blockDim.x;
   V4<T>* stage0 = (V4<T>*)(((uintptr_t)(s_scale + K) + 127) & ~(uintptr_t)127);
   const bool two = p.stages > 1;
@@ -756,7 +757,8 @@ void launch_commit_rho(Ctx& c) {
 template <typename T>
 static size_t sweep_smem(int K, int threads, int stages) {
   size_t b = (sizeof(int) + sizeof(float)) * (size_t)K;
-  if (sizeof(T) == 4) b = ((b + 127) & ~(size_t)127) + (size_t)stages * kTileV4 * threads * sizeof(V4<T>) + 16 + 128;
+  if (sizeof(T) == 4 && stages > 0)
+    b = ((b + 127) & ~(size_t)127) + (size_t)stages * kTileV4 * threads * sizeof(V4<T>) + 16 + 128;
   return b;
 }
 
