@@ -439,32 +439,49 @@ __device__ __forceinline__ void seg_scan(int bus, T* S) {
   }
 }
 
-// one task of at most 32 entries; all 32 lanes call it
+// the loads of one task of at most 32 entries: this lane's coupling, and for
+// the last lane of each bus its load and shunts (issued before any is used)
 template <typename T>
-__device__ __forceinline__ void bus_task(const SweepP<T>& p, Slot s, int slot, const int* s_done) {
-  const Dev& d = p.d;
+struct TaskData {
+  Slot s;
+  bool last;
+  V4<T> x, lm, zo, br;
+  T r;
+  int isref;
+};
+
+template <typename T>
+__device__ __forceinline__ TaskData<T> task_load(const Dev& d, Slot s, const int* s_done) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  int bus = s.bus, inst = s.inst;
-  if (bus >= 0 && s_done[inst]) bus = inst = -1;
-  const int bnext = __shfl_down_sync(FULL, bus, 1);
-  const bool last = bus >= 0 && (lane == 31 || bnext != bus);
-  V4<T> x = {0, 0, 0, 0}, lm = {0, 0, 0, 0}, zo = {0, 0, 0, 0};
-  T r = T(1);
-  V4<T> br = {0, 0, 0, 0};
-  int isref = 0;
-  // every load of the task is issued here, before any is used
-  if (bus >= 0) entry_load(d, s.code, x, lm, zo, r);
-  if (last) {
-    br = ((const V4<T>*)d.brec)[bus];  // pdk qdk gs bs
-    isref = d.isref[bus];
+  TaskData<T> a;
+  if (s.bus >= 0 && s_done[s.inst]) s.bus = s.inst = -1;
+  a.s = s;
+  const int bnext = __shfl_down_sync(FULL, s.bus, 1);
+  a.last = s.bus >= 0 && (lane == 31 || bnext != s.bus);
+  a.x = a.lm = a.zo = a.br = {T(0), T(0), T(0), T(0)};
+  a.r = T(1);
+  a.isref = 0;
+  if (s.bus >= 0) entry_load(d, s.code, a.x, a.lm, a.zo, a.r);
+  if (a.last) {
+    a.br = ((const V4<T>*)d.brec)[s.bus];  // pdk qdk gs bs
+    a.isref = d.isref[s.bus];
   }
+  return a;
+}
+
+// one task of at most 32 entries from its loaded data; all 32 lanes call it
+template <typename T>
+__device__ __forceinline__ void bus_task(const Dev& d, const TaskData<T>& a, int slot) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int bus = a.s.bus;
   T S[6] = {0, 0, 0, 0, 0, 0};
-  if (bus >= 0) entry_sums(s.code, x, lm, r, S);
+  if (bus >= 0) entry_sums(a.s.code, a.x, a.lm, a.r, S);
   seg_scan(bus, S);
   T n1 = 0, n2 = 0, dw = 0, dth = 0;
-  if (last) bus_solve(d, bus, br, isref, S, n1, n2, dw, dth);
-  const unsigned after = __ballot_sync(FULL, last) >> lane;
+  if (a.last) bus_solve(d, bus, a.br, a.isref, S, n1, n2, dw, dth);
+  const unsigned after = __ballot_sync(FULL, a.last) >> lane;
   const int src = after ? lane + __ffs(after) - 1 : lane;
   n1 = __shfl_sync(FULL, n1, src);
   n2 = __shfl_sync(FULL, n2, src);
@@ -472,12 +489,12 @@ __device__ __forceinline__ void bus_task(const SweepP<T>& p, Slot s, int slot, c
   dth = __shfl_sync(FULL, dth, src);
   T rm = T(0), sm = T(0);
   if (bus >= 0) {
-    entry_update(d, s.code, x, lm, zo, r, n1, n2, dw, dth, rm, sm);
+    entry_update(d, a.s.code, a.x, a.lm, a.zo, a.r, n1, n2, dw, dth, rm, sm);
     // a NaN must not pass the residual test
     if (!(rm == rm)) rm = T(1e30);
     if (!(sm == sm)) sm = T(1e30);
   }
-  res_max2(d.res_slots, d.K, slot, rm, sm, inst);
+  res_max2(d.res_slots, d.K, slot, rm, sm, a.s.inst);
 }
 
 // one bus with more than 32 entries (entries [q0, q1) of ent); lanes loop
@@ -631,17 +648,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sweep(SweepP<T>
     if (prof) { tp1 = gtimer(); atomicAdd(&d.phase_ns[0], tp1 - tp0); }
     if (!grid_barrier(d.bar, d.err, p.spin_limit)) { aborted = true; break; }
     if (prof) { tp0 = gtimer(); atomicAdd(&d.phase_ns[1], tp0 - tp1); }
-    // phase B: buses, one warp task (consecutive whole buses) at a time, the
-    // next task's slots loaded while the current one is solved; loop bounds
-    // are uniform per warp so that all lanes reduce together
+    // phase B: buses, one warp task (consecutive whole buses) at a time in a
+    // two-deep pipeline: while task t is solved, the couplings of task t + 1
+    // and the slots of task t + 2 are in flight (every entry belongs to one
+    // task, so the loads ahead never read what the current task writes);
+    // loop bounds are uniform per warp so that all lanes reduce together
     {
       const int lane = threadIdx.x & 31, wid = tid >> 5, nw = nthreads >> 5;
-      Slot nxt = {-1, 0, -1};
-      if (wid < d.NT) nxt = load_slot(d, wid, lane);
+      const Slot none = {-1, 0, -1};
+      Slot s1 = wid + nw < d.NT ? load_slot(d, wid + nw, lane) : none;
+      TaskData<T> cur = task_load<T>(d, wid < d.NT ? load_slot(d, wid, lane) : none, s_done);
       for (int t = wid; t < d.NT; t += nw) {
-        const Slot cur = nxt;
-        if (t + nw < d.NT) nxt = load_slot(d, t + nw, lane);
-        bus_task(p, cur, slot, s_done);
+        const Slot s2 = t + 2 * nw < d.NT ? load_slot(d, t + 2 * nw, lane) : none;
+        const TaskData<T> nxt = task_load<T>(d, s1, s_done);
+        bus_task(d, cur, slot);
+        cur = nxt;
+        s1 = s2;
       }
       for (int b = wid; b < d.NBIG; b += nw) bus_task_big(p, d.big[2 * b], d.big[2 * b + 1], slot, s_done);
     }
