@@ -177,10 +177,35 @@ def measure(args, grid, precision, steps, warmup, local_rank, world, dev, with_e
     return out
 
 
+def replica_grid(rank, world):
+    """The instance a rank solves: the 2,000-bus grid on one GPU; with N ranks,
+    replicas of it under N correlated load scenarios, one per rank (weak
+    scaling, no data-path collective)."""
+    from paper_2310_13143_gb300 import gridgen
+
+    grid = gridgen.grid_2000bus()
+    if world > 1:
+        grid = gridgen.scenarios_rff(grid, world, seed=4000)[rank]
+    return grid
+
+
+def combine_ranks(total_s, conv, admm_iters, world, dev):
+    """Job totals over ranks: the slowest rank's time, the sum of converged
+    solves and of ADMM iterations."""
+    import torch
+
+    t = torch.tensor([total_s, conv, admm_iters], dtype=torch.float64)
+    if world > 1:
+        tt = t.to(dev)
+        torch.distributed.all_reduce(tt[0:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tt[1:3], op=torch.distributed.ReduceOp.SUM)
+        t = tt.cpu()
+    return float(t[0]), int(t[1]), int(t[2])
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
 
-    from paper_2310_13143_gb300 import gridgen
     from paper_2310_13143_gb300.build import build
 
     if rank == 0:
@@ -189,9 +214,7 @@ def run_gpu(args, rank, world, local_rank):
         torch.distributed.barrier()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    grid = gridgen.grid_2000bus()
-    if world > 1:  # replicas: every rank gets its own load scenario
-        grid = gridgen.scenarios_rff(grid, world, seed=4000)[rank]
+    grid = replica_grid(rank, world)
 
     m = measure(args, grid, args.precision, args.steps, args.warmup, local_rank, world, dev,
                 with_e2e=not args.no_e2e, with_clocks=True)
@@ -200,13 +223,7 @@ def run_gpu(args, rank, world, local_rank):
         plain = measure(args, grid, "fp64", max(2, args.steps // 2), args.warmup, local_rank, world, dev,
                         with_e2e=False, with_clocks=False)
 
-    t = torch.tensor([m["total_s"], m["conv"], m["admm_iters"]], dtype=torch.float64)
-    if world > 1:
-        tt = t.to(dev)
-        torch.distributed.all_reduce(tt[0:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt[1:3], op=torch.distributed.ReduceOp.SUM)
-        t = tt.cpu()
-    total_s, conv_all, iters_all = float(t[0]), int(t[1]), int(t[2])
+    total_s, conv_all, iters_all = combine_ranks(m["total_s"], m["conv"], m["admm_iters"], world, dev)
     if rank != 0:
         return None
     hbm, which = _peaks()
