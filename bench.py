@@ -284,7 +284,7 @@ def run_gpu(args, rank, world, local_rank):
                              "avg_sweep_launch_ms": plain["prof"]["sweep_ms"] / max(plain["prof"]["sweeps"], 1)}
     if world == 1 and not args.no_batched:
         bgrids = workload_grids("batched")
-        out["batched_sweep"] = sweep_only(bgrids, args.precision, 50, 3, 1)
+        out["batched_sweep"] = sweep_only(bgrids, args.precision, 50, 3, 1, workload="batched")
         out["batched_sweep"]["workload"] = ("256 correlated load scenarios of the 2,000-bus grid + 64 grids of "
                                             "118-10,000 buses (log-uniform), one persistent launch, ADMM sweep only")
         out["batched_solve"] = batched_solve(bgrids)
@@ -468,7 +468,27 @@ def workload_grids(name):
     raise ValueError(name)
 
 
-def sweep_only(grids, precision, iters, launches, warmup):
+def measured_traffic(workload, iters_per_launch):
+    """DRAM bytes per launch of the FP32 sweep on a workload, from the ncu
+    record in profiles/k_sweep_traffic.json, scaled by iterations per launch;
+    None when no record exists or the sweep's sources changed since."""
+    import hashlib
+
+    try:
+        with open(os.path.join(HERE, "profiles", "k_sweep_traffic.json")) as f:
+            rec = json.load(f)["records"][workload]
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(HERE, src), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != rec["sha256"]:
+            return None
+        return rec["dram_bytes_per_iter"] * iters_per_launch
+    except Exception:
+        return None
+
+
+def sweep_only(grids, precision, iters, launches, warmup, workload=None):
     """ADMM sweep alone (fixed iteration count) on the QP at the flat start:
     ADMM iterations/s and the sweep's HBM roofline on a given workload."""
     import torch
@@ -497,7 +517,9 @@ def sweep_only(grids, precision, iters, launches, warmup):
     return {"instances": len(grids), "buses": B, "branches": L, "generators": G, "precision": precision,
             "us_per_iter": us, "admm_iter_per_s": 1e6 / us, "instance_iters_per_s": len(grids) * 1e6 / us,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                         "traffic": None, "peak_source": which, "bytes_per_iter": bpi,
+                         "traffic": measured_traffic(workload, iters) if precision == "mixed" and workload else None,
+                         "traffic_unit": "bytes per launch", "iters_per_launch": iters,
+                         "peak_source": which, "bytes_per_iter": bpi, "bytes_per_launch": bpi * iters,
                          "kernel": "k_sweep<float>" if precision == "mixed" else "k_sweep<double>"}}
 
 
@@ -606,7 +628,8 @@ def main():
         import torch
 
         torch.cuda.set_device(local_rank)
-        r = sweep_only(workload_grids(args.workload), args.precision, args.sweep_iters, args.steps, args.warmup)
+        r = sweep_only(workload_grids(args.workload), args.precision, args.sweep_iters, args.steps, args.warmup,
+                       workload=args.workload)
         r.update({"metric": "ADMM iter/s (sweep only)", "value": r["admm_iter_per_s"], "unit": "iter/s",
                   "workload": args.workload, "steps": args.steps, "warmup": args.warmup})
         if rank == 0:
