@@ -89,9 +89,11 @@ acopf_status acopf_mlp_sync(acopf_mlp_handle h);
  * C [M x N] = A [M x K] * B [N x K]^T with A, B bfloat16 (row stride K, K a
  * multiple of 8, 16-byte aligned) and C FP32 (row stride N), all device
  * memory; the contraction is split into at most `splits` slices summed in
- * FP32.  Allocates scratch, synchronises the stream. */
+ * FP32.  Allocates scratch, synchronises the stream.  If ms is not NULL it
+ * receives the device time of the product's kernels (CUDA events recorded on
+ * the stream around them). */
 acopf_status acopf_gemm_bf16(const void* A, const void* B, float* C, int32_t M, int32_t N, int32_t K, int32_t splits,
-                             void* cuda_stream);
+                             void* cuda_stream, float* ms);
 
 /* Warm start of every instance of a solver handle from device predictions:
  * pred [K x ld] FP32 (K = number of instances; ld >= the width below), row k

@@ -141,7 +141,7 @@ def lib():
             "acopf_mlp_train_step": (S, [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p]),
             "acopf_mlp_sync": (S, [H]),
             "acopf_gemm_bf16": (S, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
-                                    C.c_void_p]),
+                                    C.c_void_p, FP]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -400,11 +400,13 @@ class Solver:
 
 def gemm_bf16(a_ptr: int, b_ptr: int, c_ptr: int, M: int, N: int, K: int, splits: int = 1, stream: int = 0):
     """C [M x N] = A [M x K] B [N x K]^T on the tensor cores (device pointers:
-    bfloat16 A and B, FP32 C)."""
+    bfloat16 A and B, FP32 C).  Returns the kernels' device time in ms."""
+    ms = C.c_float()
     st = lib().acopf_gemm_bf16(C.c_void_p(a_ptr), C.c_void_p(b_ptr), C.c_void_p(c_ptr), M, N, K, splits,
-                               C.c_void_p(stream))
+                               C.c_void_p(stream), C.byref(ms))
     if st != 0:
         raise AcopfError(st, "acopf_gemm_bf16 failed")
+    return ms.value
 
 
 class Mlp:

@@ -7,14 +7,16 @@
 //
 //   C[M x N] = A[M x K] * B[N x K]^T,   A, B bfloat16, K contiguous,
 //
-// with 128 x 128 output tiles.  One thread streams 128 x 64 operand tiles
-// into shared memory with TMA (cp.async.bulk.tensor, 128-byte swizzle, four
-// stages completed on mbarriers), one thread issues tcgen05.mma (kind::f16,
-// BF16 x BF16 -> FP32) into a 128-column tensor-memory accumulator, and the
-// four warps read the accumulator back with tcgen05.ld for a fused epilogue
-// (bias, GELU, GELU derivative, standardisation, bfloat16 row-major and
-// transposed stores).  Long contractions are split over K (grid z) into FP32
-// partial tiles summed by k_splitk.
+// with 128 x 256 output tiles in a persistent, warp-specialised kernel: one
+// CTA per SM loops over tiles; warp 0 streams 128 x 64 and 256 x 64 operand
+// tiles into a four-stage shared-memory ring with TMA (cp.async.bulk.tensor,
+// 128-byte swizzle, completion counted on mbarriers); warp 1 issues
+// tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, 128 x 256 x 16) into one of two
+// 256-column tensor-memory accumulators; warps 2-5 read the other accumulator
+// back with tcgen05.ld for a fused epilogue (bias, GELU, GELU derivative,
+// bfloat16 row-major and transposed stores), so the epilogue of one tile
+// overlaps the main loop of the next.  Long contractions are split over K
+// into FP32 partial tiles summed by k_splitk.
 //
 // Layout convention: the backward pass needs every operand with its
 // contraction index contiguous, so the forward epilogue stores each hidden
@@ -41,11 +43,12 @@ namespace nn {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
-constexpr uint32_t kTileBytes = BM * BK * 2;  // one operand tile: 128 rows x 128 bytes
-constexpr int kGemmThreads = 128;
-constexpr size_t kGemmSmem = 1024 + (size_t)STAGES * 2 * kTileBytes + 256;
-constexpr uint32_t kTmemCols = 128;
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr uint32_t kABytes = BM * BK * 2;  // A tile: 128 rows x 128 bytes
+constexpr uint32_t kBBytes = BN * BK * 2;  // B tile: 256 rows x 128 bytes
+constexpr int kGemmThreads = 192;          // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr size_t kGemmSmem = 1024 + (size_t)STAGES * (kABytes + kBBytes) + 256;
+constexpr uint32_t kTmemCols = 512;        // two 256-column FP32 accumulators
 
 // Instruction descriptor of tcgen05.mma kind::f16: D in FP32 (bits 4-5 = 1),
 // A and B bfloat16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
@@ -179,33 +182,106 @@ __device__ __forceinline__ void epi_one(const Epi& e, int m, int n, float acc, i
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+
+// 16 consecutive accumulator columns [n, n + 16) of row m: vector stores when
+// the whole group is in range, the per-element epilogue otherwise
+__device__ __forceinline__ void epi_store16(const Epi& e, int m, int n, const float v[16], int split) {
+  if (m >= e.M) return;
+  if (n + 16 > e.N) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) epi_one(e, m, n + j, v[j], split);
+    return;
+  }
+  switch (e.op) {
+    case EPI_F32:
+    case EPI_PARTIAL: {
+      float* dst = e.op == EPI_PARTIAL ? e.f32 + (size_t)split * e.split_stride + (size_t)m * e.ld_f32 + n
+                                       : e.f32 + (size_t)m * e.ld_f32 + n;
+      float w[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        float x = v[j];
+        if (e.op == EPI_F32) {
+          if (e.bias) x += e.bias[n + j];
+          if (e.scale) x = x * e.scale[n + j] + e.shift[n + j];
+        }
+        w[j] = x;
+      }
+      if (((uintptr_t)dst & 15) == 0) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) *(float4*)(dst + j) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) dst[j] = w[j];
+      }
+      break;
+    }
+    case EPI_GELU:
+    case EPI_GELU_BWD: {
+      bf16 h[16];
+      if (e.op == EPI_GELU) {
+        float* zd = e.f32 + (size_t)m * e.ld_f32 + n;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float zz = v[j] + e.bias[n + j];
+          zd[j] = zz;
+          h[j] = __float2bfloat16_rn(m < e.rows_valid ? gelu_f(zz) : 0.0f);
+        }
+      } else {
+        const float* zs = e.z + (size_t)m * e.ld_z + n;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) h[j] = __float2bfloat16_rn(m < e.rows_valid ? v[j] * gelu_grad_f(zs[j]) : 0.0f);
+      }
+      bf16* dst = e.bf + (size_t)m * e.ld_bf + n;
+      if (((uintptr_t)dst & 15) == 0) {
+        *(uint4*)dst = *(const uint4*)&h[0];
+        *(uint4*)(dst + 8) = *(const uint4*)&h[8];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) dst[j] = h[j];
+      }
+      // transposed: lanes hold consecutive rows, so each column's stores coalesce
+#pragma unroll
+      for (int j = 0; j < 16; ++j) e.bt[(size_t)(n + j) * e.ld_bt + m] = h[j];
+      break;
+    }
+  }
+}
+
 // -------------------------------------------------------------- GEMM kernel
-// grid (ceil(N / 128), ceil(M / 128), splits); 128 threads; kGemmSmem bytes of
-// dynamic shared memory.  Split z covers K tiles [z * kts, (z + 1) * kts).
+// Persistent: grid = min(work items, SMs), 192 threads, kGemmSmem bytes of
+// dynamic shared memory.  Work item w = (split z, row block, column block);
+// split z covers K tiles [z * kts, (z + 1) * kts).  Every wait is bounded:
+// on time-out the waiting role records *err and stops.
 __global__ void __launch_bounds__(kGemmThreads, 1)
-    k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int K, int kts, Epi e,
-              int* err, long long spin) {
+    k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int K, int kts,
+              int splits, Epi e, int* err, long long spin) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
-  uint8_t* sB = smem + STAGES * kTileBytes;
-  uint64_t* full = (uint64_t*)(smem + 2 * STAGES * kTileBytes);
+  uint8_t* sB = smem + STAGES * kABytes;
+  uint64_t* full = (uint64_t*)(smem + STAGES * (kABytes + kBBytes));
   uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
-  uint32_t* tslot = (uint32_t*)(done + 1);
+  uint64_t* tfull = empty + STAGES;  // accumulator a holds a finished tile
+  uint64_t* tempty = tfull + 2;      // accumulator a has been read by the epilogue
+  uint32_t* tslot = (uint32_t*)(tempty + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int mt = (e.M + BM - 1) / BM, nt = (e.N + BN - 1) / BN;
+  const int items = splits * mt * nt;
   const int kt_total = (K + BK - 1) / BK;
-  const int kt0 = blockIdx.z * kts;
-  const int kt1 = kt0 + kts < kt_total ? kt0 + kts : kt_total;
-  const int nk = kt1 > kt0 ? kt1 - kt0 : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4);  // one arrival per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -219,53 +295,91 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  if (nk > 0 && warp == 0 && lane == 0) {
-    // producer: operand tiles into the ring of stages
-    for (int i = 0; i < nk; ++i) {
-      const int s = i % STAGES;
-      if (i >= STAGES && !mbar_wait(&empty[s], ((i / STAGES) - 1) & 1, spin)) {
-        atomicExch(err, 1);
-        break;
+  if (warp == 0) {
+    if (lane == 0) {  // producer: operand tiles into the ring of stages
+      int i = 0;
+      bool ok = true;
+      for (int w = blockIdx.x; w < items && ok; w += gridDim.x) {
+        const int z = w / (mt * nt), mb = (w / nt) % mt, nb = w % nt;
+        const int kt0 = z * kts, kt1 = kt0 + kts < kt_total ? kt0 + kts : kt_total;
+        for (int kt = kt0; kt < kt1; ++kt, ++i) {
+          const int s = i % STAGES;
+          if (i >= STAGES && !mbar_wait(&empty[s], ((i / STAGES) - 1) & 1, spin)) {
+            atomicExch(err, 1);
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], kABytes + kBBytes);
+          tma_load_2d(sA + s * kABytes, &ta, kt * BK, mb * BM, &full[s]);
+          tma_load_2d(sB + s * kBBytes, &tb, kt * BK, nb * BN, &full[s]);
+        }
       }
-      mbar_expect_tx(&full[s], 2 * kTileBytes);
-      tma_load_2d(sA + s * kTileBytes, &ta, (kt0 + i) * BK, m0, &full[s]);
-      tma_load_2d(sB + s * kTileBytes, &tb, (kt0 + i) * BK, n0, &full[s]);
     }
-  } else if (nk > 0 && warp == 1 && lane == 0) {
-    // MMA issuer: four K-steps of 16 per stage; each commit frees a stage
-    for (int i = 0; i < nk; ++i) {
-      const int s = i % STAGES;
-      if (!mbar_wait(&full[s], (i / STAGES) & 1, spin)) {
-        atomicExch(err, 1);
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      int i = 0, j = 0;
+      bool ok = true;
+      for (int w = blockIdx.x; w < items && ok; w += gridDim.x, ++j) {
+        const int z = w / (mt * nt);
+        const int kt0 = z * kts, kt1 = kt0 + kts < kt_total ? kt0 + kts : kt_total;
+        const int a = j & 1, u = j >> 1;
+        if (u >= 1 && !mbar_wait(&tempty[a], (u - 1) & 1, spin)) {
+          atomicExch(err, 1);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)(a * BN);
+        for (int kt = kt0; kt < kt1; ++kt, ++i) {
+          const int s = i % STAGES;
+          if (!mbar_wait(&full[s], (i / STAGES) & 1, spin)) {
+            atomicExch(err, 1);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t pa = saddr(sA + s * kABytes), pb = saddr(sB + s * kBBytes);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            mma_bf16(acc, sdesc(pa + 32 * kk), sdesc(pb + 32 * kk), (kt > kt0 || kk > 0) ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        if (kt1 > kt0) mma_commit(&tfull[a]);  // arrives when this tile's MMAs are done
+        else mbar_arrive(&tfull[a]);            // empty K range: nothing to wait for
+      }
+    }
+  } else {
+    // epilogue: warp w reads accumulator lanes (rows) 32 (w % 4) .. + 31
+    const int q = warp & 3;
+    int j = 0;
+    for (int w = blockIdx.x; w < items; w += gridDim.x, ++j) {
+      const int z = w / (mt * nt), mb = (w / nt) % mt, nb = w % nt;
+      const int kt0 = z * kts, kt1 = kt0 + kts < kt_total ? kt0 + kts : kt_total;
+      const int a = j & 1, u = j >> 1;
+      bool ok = mbar_wait(&tfull[a], u & 1, spin);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) atomicExch(err, 1);
         break;
       }
       tc_fence_after();
-      const uint32_t a = saddr(sA + s * kTileBytes), b = saddr(sB + s * kTileBytes);
+      const int row = mb * BM + q * 32 + lane;
+      const int n0 = nb * BN;
+      for (int c = 0; c < BN; c += 16) {
+        if (n0 + c >= e.N) break;
+        float v[16];
+        if (kt1 > kt0) {
+          tmem_ld16(tmem + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+        } else {
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) mma_bf16(tmem, sdesc(a + 32 * kk), sdesc(b + 32 * kk), (i | kk) != 0);
-      mma_commit(&empty[s]);
+          for (int t = 0; t < 16; ++t) v[t] = 0.0f;
+        }
+        epi_store16(e, row, n0 + c, v, z);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[a]);
     }
-    mma_commit(done);  // arrives once every MMA issued above has completed
-  }
-  __syncwarp();
-
-  // epilogue: warp w owns accumulator lanes (rows) 32 w .. 32 w + 31
-  bool ok = nk == 0 || mbar_wait(done, 0, spin);
-  ok = __all_sync(0xffffffffu, ok);
-  if (!ok && lane == 0) atomicExch(err, 1);
-  tc_fence_after();
-  const int row = m0 + warp * 32 + lane;
-  for (int c = 0; c < BN; c += 16) {
-    if (n0 + c >= e.N) break;
-    float v[16];
-    if (nk > 0 && ok) {
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = 0.0f;
-    }
-#pragma unroll
-    for (int j = 0; j < 16; ++j) epi_one(e, row, n0 + c + j, v[j], blockIdx.z);
   }
   tc_fence_before();
   __syncthreads();
@@ -446,13 +560,13 @@ static bool encode_fn() {
   return true;
 }
 
-// 2-D bfloat16 operand [rows x cols], row stride ld elements; boxes of 128 rows x 64 columns
-static bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld) {
+// 2-D bfloat16 operand [rows x cols], row stride ld elements; boxes of box_rows rows x 64 columns
+static bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int box_rows) {
   if (!encode_fn()) return false;
   if (((uintptr_t)base & 15) || (ld * 2) % 16 || rows < 1 || cols < 1) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, es,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -468,15 +582,16 @@ struct Gemm {
 
 static int g_smem_set = -1;
 
-static cudaError_t run_gemm(const Gemm& g, float* ws, int* err, cudaStream_t st, long long spin) {
+static cudaError_t run_gemm(const Gemm& g, float* ws, int* err, cudaStream_t st, long long spin, int sms) {
   if (g_smem_set < 0) {
     cudaError_t c = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
     if (c != cudaSuccess) return c;
     g_smem_set = 1;
   }
-  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.splits);
+  const int items = g.splits * ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
+  const int grid = items < sms ? items : sms;
   if (g.splits == 1) {
-    k_gemm_tc<<<grid, kGemmThreads, kGemmSmem, st>>>(g.ta, g.tb, g.K, g.kts, g.e, err, spin);
+    k_gemm_tc<<<grid, kGemmThreads, kGemmSmem, st>>>(g.ta, g.tb, g.K, g.kts, 1, g.e, err, spin);
     return cudaGetLastError();
   }
   Epi p = g.e;
@@ -484,7 +599,7 @@ static cudaError_t run_gemm(const Gemm& g, float* ws, int* err, cudaStream_t st,
   p.f32 = ws;
   p.ld_f32 = g.N;
   p.split_stride = (size_t)g.M * g.N;
-  k_gemm_tc<<<grid, kGemmThreads, kGemmSmem, st>>>(g.ta, g.tb, g.K, g.kts, p, err, spin);
+  k_gemm_tc<<<grid, kGemmThreads, kGemmSmem, st>>>(g.ta, g.tb, g.K, g.kts, g.splits, p, err, spin);
   size_t total = (size_t)g.M * g.N;
   k_splitk<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(ws, g.splits, p.split_stride, g.e);
   return cudaGetLastError();
@@ -569,7 +684,7 @@ static bool plan(Net* n) {
     // forward: [Mb x in] * W[out x in]^T
     Gemm& f = n->fwd[l];
     f.M = Mb; f.N = out; f.K = in;
-    if (!make_map(&f.ta, n->A[l], Mb, in, in) || !make_map(&f.tb, y.W16, out, in, in)) return false;
+    if (!make_map(&f.ta, n->A[l], Mb, in, in, BM) || !make_map(&f.tb, y.W16, out, in, in, BN)) return false;
     memset(&f.e, 0, sizeof(Epi));
     f.e.M = Mb; f.e.N = out; f.e.rows_valid = Mb; f.e.bias = y.b;
     if (l < nl - 1) {
@@ -586,7 +701,7 @@ static bool plan(Net* n) {
     // weight gradient: dW = D^T [out x Mb] * (A^T [in x Mb])^T
     Gemm& w = n->bwd_w[l];
     w.M = out; w.N = in; w.K = Mb;
-    if (!make_map(&w.ta, n->DT[l + 1], out, Mb, Mb) || !make_map(&w.tb, n->AT[l], in, Mb, Mb)) return false;
+    if (!make_map(&w.ta, n->DT[l + 1], out, Mb, Mb, BM) || !make_map(&w.tb, n->AT[l], in, Mb, Mb, BN)) return false;
     memset(&w.e, 0, sizeof(Epi));
     w.e.op = EPI_F32; w.e.M = out; w.e.N = in; w.e.rows_valid = out;
     w.e.f32 = y.gW; w.e.ld_f32 = in;
@@ -596,7 +711,7 @@ static bool plan(Net* n) {
       // input gradient: D_l = (D_{l+1} [Mb x out] * (W16T [in x out])^T) * GELU'(Z_l)
       Gemm& x = n->bwd_x[l];
       x.M = Mb; x.N = in; x.K = out;
-      if (!make_map(&x.ta, n->D[l + 1], Mb, out, out) || !make_map(&x.tb, y.W16T, in, out, out)) return false;
+      if (!make_map(&x.ta, n->D[l + 1], Mb, out, out, BM) || !make_map(&x.tb, y.W16T, in, out, out, BN)) return false;
       memset(&x.e, 0, sizeof(Epi));
       x.e.op = EPI_GELU_BWD; x.e.M = Mb; x.e.N = in; x.e.rows_valid = Mb;
       x.e.z = n->Z[l]; x.e.ld_z = in;
@@ -632,7 +747,7 @@ static acopf_status forward(Net* n, int rows) {
   for (int l = 0; l < n->nl; ++l) {
     Gemm g = n->fwd[l];
     g.e.rows_valid = rows;
-    NCK(run_gemm(g, n->ws, n->err, n->stream, n->spin));
+    NCK(run_gemm(g, n->ws, n->err, n->stream, n->spin, n->sms));
   }
   return ACOPF_OK;
 }
@@ -862,10 +977,10 @@ acopf_status acopf_mlp_train_step(acopf_mlp_handle h, const float* X, const floa
   k_sum<<<1, 32, 0, n->stream>>>(n->part, n->nparts, 1.0 / ((double)rows * dn), n->loss);
   NCK(cudaGetLastError());
   for (int l = nl - 1; l >= 0; --l) {
-    NCK(run_gemm(n->bwd_w[l], n->ws, n->err, n->stream, n->spin));
+    NCK(run_gemm(n->bwd_w[l], n->ws, n->err, n->stream, n->spin, n->sms));
     k_colsum<<<(n->dims[l + 1] + 127) / 128, 128, 0, n->stream>>>(n->D[l + 1], Mb, n->dims[l + 1], n->L[l].gb);
     NCK(cudaGetLastError());
-    if (l >= 1) NCK(run_gemm(n->bwd_x[l], n->ws, n->err, n->stream, n->spin));
+    if (l >= 1) NCK(run_gemm(n->bwd_x[l], n->ws, n->err, n->stream, n->spin, n->sms));
   }
   n->step += 1;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
@@ -891,12 +1006,12 @@ acopf_status acopf_mlp_sync(acopf_mlp_handle h) {
 // C[M x N] = A[M x K] B[N x K]^T: bfloat16 operands (row stride K), FP32 output
 // (row stride N), all device pointers; on the given stream, synchronised.
 acopf_status acopf_gemm_bf16(const void* A, const void* B, float* C, int32_t M, int32_t N, int32_t K, int32_t splits,
-                             void* stream) {
+                             void* stream, float* ms) {
   if (!A || !B || !C || M < 1 || N < 1 || K < 8 || K % 8) return ACOPF_EINVAL;
   Gemm g;
   memset(&g, 0, sizeof(g));
   g.M = M; g.N = N; g.K = K;
-  if (!make_map(&g.ta, A, M, K, K) || !make_map(&g.tb, B, N, K, K)) return ACOPF_EINVAL;
+  if (!make_map(&g.ta, A, M, K, K, BM) || !make_map(&g.tb, B, N, K, K, BN)) return ACOPF_EINVAL;
   int kt = (K + BK - 1) / BK;
   int s = splits < 1 ? 1 : (splits > kt ? kt : splits);
   g.kts = (kt + s - 1) / s;
@@ -911,10 +1026,26 @@ acopf_status acopf_gemm_bf16(const void* A, const void* B, float* C, int32_t M, 
     cudaFree(err);
     return ACOPF_ENOMEM;
   }
-  cudaError_t e = run_gemm(g, ws, err, st, 1ll << 32);
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ms) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+  }
+  cudaError_t e = run_gemm(g, ws, err, st, 1ll << 32, sms);
+  if (ms) cudaEventRecord(e1, st);
   int hv = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hv, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (ms) {
+    *ms = 0.0f;
+    if (e == cudaSuccess) cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
   if (ws) cudaFree(ws);
   cudaFree(err);
   if (e != cudaSuccess) return ACOPF_ECUDA;
