@@ -251,6 +251,21 @@ __device__ __forceinline__ void epi_store16(const Epi& e, int m, int n, const fl
   }
 }
 
+// work item w -> (split z, row block mb, column block nb).  Within a split,
+// items run through groups of kGroup row blocks, column-block-major inside a
+// group, so the tiles in flight at one time share a few A and B blocks in L2.
+constexpr int kGroup = 16;
+__device__ __forceinline__ void decode_item(int w, int mt, int nt, int& z, int& mb, int& nb) {
+  z = w / (mt * nt);
+  const int r = w - z * mt * nt;
+  const int g = r / (kGroup * nt);
+  const int g0 = g * kGroup;
+  const int gm = mt - g0 < kGroup ? mt - g0 : kGroup;  // row blocks in this group
+  const int rr = r - g0 * nt;
+  mb = g0 + rr % gm;
+  nb = rr / gm;
+}
+
 // -------------------------------------------------------------- GEMM kernel
 // Persistent: grid = min(work items, SMs), 192 threads, kGemmSmem bytes of
 // dynamic shared memory.  Work item w = (split z, row block, column block);
@@ -300,7 +315,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       int i = 0;
       bool ok = true;
       for (int w = blockIdx.x; w < items && ok; w += gridDim.x) {
-        const int z = w / (mt * nt), mb = (w / nt) % mt, nb = w % nt;
+        int z, mb, nb;
+        decode_item(w, mt, nt, z, mb, nb);
         const int kt0 = z * kts, kt1 = kt0 + kts < kt_total ? kt0 + kts : kt_total;
         for (int kt = kt0; kt < kt1; ++kt, ++i) {
           const int s = i % STAGES;
@@ -320,7 +336,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       int i = 0, j = 0;
       bool ok = true;
       for (int w = blockIdx.x; w < items && ok; w += gridDim.x, ++j) {
-        const int z = w / (mt * nt);
+        const int z = w / (mt * nt);  // the MMA issuer only needs the split
         const int kt0 = z * kts, kt1 = kt0 + kts < kt_total ? kt0 + kts : kt_total;
         const int a = j & 1, u = j >> 1;
         if (u >= 1 && !mbar_wait(&tempty[a], (u - 1) & 1, spin)) {
@@ -353,7 +369,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const int q = warp & 3;
     int j = 0;
     for (int w = blockIdx.x; w < items; w += gridDim.x, ++j) {
-      const int z = w / (mt * nt), mb = (w / nt) % mt, nb = w % nt;
+      int z, mb, nb;
+        decode_item(w, mt, nt, z, mb, nb);
       const int kt0 = z * kts, kt1 = kt0 + kts < kt_total ? kt0 + kts : kt_total;
       const int a = j & 1, u = j >> 1;
       bool ok = mbar_wait(&tfull[a], u & 1, spin);
