@@ -265,7 +265,10 @@ def run_gpu(args, rank, world, local_rank):
         "primal_last": last["primal"],
         "dual_last": last["dual"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "peak_source": which,
+                     "frac": achieved / hbm,
+                     "traffic": (measured_traffic("syn2000", iters_per_launch)
+                                 if args.precision == "mixed" and world == 1 else None),
+                     "traffic_unit": "bytes per launch", "peak_source": which,
                      "kernel": "k_sweep<float>" if args.precision == "mixed" else "k_sweep<double>",
                      "bytes_per_iter": bpi, "iters_per_launch": iters_per_launch, "avg_launch_ms": avg_ms},
         "gpu_launches": m["launches"],
@@ -282,6 +285,8 @@ def run_gpu(args, rank, world, local_rank):
                              "ms_per_step": 1e3 * ps / nst, "admm_iter_per_s": plain["admm_iters"] / ps,
                              "objective": plain["obj"], "objective_rel_diff_vs_mixed": abs(plain["obj"] - m["obj"]) / abs(plain["obj"]),
                              "avg_sweep_launch_ms": plain["prof"]["sweep_ms"] / max(plain["prof"]["sweeps"], 1)}
+    if world == 1 and not args.no_rho_sweep:
+        out["rho_sweep"] = rho_sweep(grid, args.precision)
     if world == 1 and not args.no_batched:
         bgrids = workload_grids("batched")
         out["batched_sweep"] = sweep_only(bgrids, args.precision, 50, 3, 1, workload="batched")
@@ -297,6 +302,38 @@ def run_gpu(args, rank, world, local_rank):
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(grid, iters_all / max(args.steps, 1), args.cpu_seconds)
     return out
+
+
+def rho_sweep(grid, precision, rhos=(2e3, 5e3, 1e4, 2e4, 5e4), reps=3):
+    """The same solve under other ADMM penalties (the paper tunes rho per case,
+    Tables I-II): solves/s, iterations and the objective for each; the
+    headline keeps the paper's large-case 2e4."""
+    import torch
+
+    from paper_2310_13143_gb300 import binding
+
+    stream = torch.cuda.Stream()
+    rows = []
+    for rho in rhos:
+        opts = binding.default_sqp(tol=1e-4, max_sqp=40, admm=dict(rho=rho, max_iter=1000, eps=1e-3,
+                                                                   eps_dual=5e-3 if precision == "mixed" else 0.0))
+        s = binding.Solver(grid, precision=precision)
+        s.set_stream(stream.cuda_stream)
+        s.sqp_solve(opts)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        conv = 0
+        a.record(stream)
+        for _ in range(reps):
+            s.sqp_solve(opts)
+            r = s.get_residuals(0)
+            conv += int(r["result_name"] == "converged" and r["primal"] <= 1e-4 and r["dual"] <= 1e-4)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        rows.append({"rho": rho, "solves_per_s": conv / t, "converged": conv, "of": reps, "ms_per_solve": 1e3 * t / reps,
+                     "sqp_iters": r["sqp_iter"], "admm_iters": r["admm_iter"], "objective": s.get_solution(0)["obj"]})
+        s.close()
+    return rows
 
 
 def batched_solve(grids, plain_sample=8):
@@ -597,6 +634,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-rho-sweep", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--workload", default="syn2000", choices=["syn2000", "batched", "syn70k", "syn70k_x16", "gemm"])
     ap.add_argument("--gemm-shape", default="8192,8192,8192")
