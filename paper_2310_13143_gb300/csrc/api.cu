@@ -1222,13 +1222,11 @@ acopf_status acopf_set_warm_start(acopf_handle h, int32_t inst, const double* x0
   }
   if (lambda0) {
     int nl = c->h_br_off[inst + 1] - c->h_br_off[inst];
-    int ng = c->h_gen_off[inst + 1] - c->h_gen_off[inst];
     acopf_admm_state st;
     memset(&st, 0, sizeof(st));
     st.lam = (double*)lambda0;
     st.lg = (double*)(lambda0 + 8 * (size_t)nl);
     if ((s = acopf_set_admm_state(h, inst, &st))) return s;
-    (void)ng;
     c->warm_lam = true;
   }
   if (rho) {

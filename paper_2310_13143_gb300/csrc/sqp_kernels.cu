@@ -848,7 +848,6 @@ __global__ void __launch_bounds__(256) k_kkt_decide(Dev d) {
   __shared__ double a[1], bsh[1], gg[2];
   if (c.accept_last) {
     const int op1[1] = {1};
-    const int op2[2] = {1, 1};
     seg_reduce<1>(d.tbr + 7 * (size_t)d.L, d.L, d.br_off[k], d.br_off[k + 1], op1, a);
     seg_reduce<1>(d.tbus + 3 * (size_t)d.B, d.B, d.bus_off[k], d.bus_off[k + 1], op1, bsh);
     // rows 0 (|f'|) and 7 (generator residual) of tgen
