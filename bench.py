@@ -425,34 +425,46 @@ def learned_warm_start(args, ntrain=4096, ntest=512, steps=2000, batch=256):
     test = scen[ntrain:]
     stream = torch.cuda.Stream()
     res = {}
-    for mode in ("cold", "warm"):
-        s = binding.Solver(test, precision="mixed")
-        s.set_stream(stream.cuda_stream)
-        s.sqp_solve_graph(opts, check_every=2)  # warm-up of the handle (graph capture)
-        pred = torch.zeros((ntest, dims[-1]), device="cuda")
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(stream)
-        if mode == "warm":
-            net.set_stream(stream.cuda_stream)
-            net.forward(Xd[ntrain:].data_ptr(), ntest, pred.data_ptr())
-            s.set_warm_start_device(pred.data_ptr(), dims[-1], base_rho=2e4, use_rho=False)
-        s.sqp_solve_graph(opts, check_every=2)
-        b.record(stream)
-        torch.cuda.synchronize()
-        rs = [s.get_residuals(k) for k in range(ntest)]
-        ob = np.array([s.get_solution(k)["obj"] for k in range(ntest)])
-        ok = [r["result_name"] == "converged" and r["primal"] <= 1e-4 and r["dual"] <= 1e-4 for r in rs]
-        res[mode] = {"seconds": a.elapsed_time(b) / 1e3, "converged": int(sum(ok)),
-                     "admm_iters_mean": float(np.mean([r["admm_iter"] for r in rs])),
-                     "sqp_iters_mean": float(np.mean([r["sqp_iter"] for r in rs])), "obj": ob}
-        s.close()
+    # cold: one handle, every held-out scenario from a flat start
+    s = binding.Solver(test, precision="mixed")
+    s.set_stream(stream.cuda_stream)
+    s.sqp_solve_graph(opts, check_every=2)  # warm-up of the handle (graph capture)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.sqp_solve_graph(opts, check_every=2)
+    torch.cuda.synchronize()
+    t_cold = time.perf_counter() - t0
+    rs = [s.get_residuals(k) for k in range(ntest)]
+    res["cold"] = {"seconds": t_cold, "rs": rs, "obj": np.array([s.get_solution(k)["obj"] for k in range(ntest)]),
+                   "fallback": 0}
+    s.close()
+    # warm: the network's prediction, then cold solves of any instance that
+    # fails the convergence test (inference, the scatter, the solve and the
+    # fallback inside the timed region, on a handle prepared like the cold one)
+    s = binding.Solver(test, precision="mixed")
+    s.set_stream(stream.cuda_stream)
+    s.sqp_solve_graph(opts, check_every=2)  # warm-up of the handle (graph capture)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rs, ob, failed = ws.solve_warm_with_fallback(s, test, net, Xd[ntrain:], opts, stream_ptr=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t_warm = time.perf_counter() - t0
+    s.close()
+    res["warm"] = {"seconds": t_warm, "rs": rs, "obj": np.array(ob), "fallback": len(failed)}
+    for m in res:
+        rsm = res[m].pop("rs")
+        ok = [ws.converged(r) for r in rsm]
+        res[m].update({"converged": int(sum(ok)), "admm_iters_mean": float(np.mean([r["admm_iter"] for r in rsm])),
+                       "sqp_iters_mean": float(np.mean([r["sqp_iter"] for r in rsm]))})
     net.close()
     okc = res["cold"]["obj"]
     rel = np.abs(res["warm"]["obj"] - okc) / np.abs(okc)
     for m in res:
         res[m].pop("obj")
         res[m]["solves_per_s"] = res[m]["converged"] / res[m]["seconds"]
+    res["cold"]["timing"] = "host wall clock of sqp_solve_graph on a prepared handle"
+    res["warm"]["timing"] = ("host wall clock of inference, scatter and sqp_solve_graph on a prepared handle, plus "
+                             "the cold fallback (new handle) of instances that failed the convergence test")
     return {"train_scenarios": ntrain, "held_out": ntest, "net": dims, "train_steps": steps, "batch": batch,
             "data_seconds": t_data, "train_seconds": t_train, "data_converged": int(conv.sum()),
             "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-10:].mean()),

