@@ -397,7 +397,7 @@ def batched_solve(grids, plain_sample=8):
                         "one handle, SQP to 1e-4 (max 40 SQP iterations, 1,000 ADMM iterations per QP)"}
 
 
-def learned_warm_start(args, ntrain=4096, ntest=512, steps=2000, batch=256):
+def learned_warm_start(args, ntrain=4096, ntest=512, steps=6000, batch=256, lr=3e-3):
     """Config 4: the warm-start network trained on cold solves of sampled
     loads of the 2,000-bus grid and judged on held-out scenarios against
     cold starts of the same scenarios."""
@@ -420,7 +420,7 @@ def learned_warm_start(args, ntrain=4096, ntest=512, steps=2000, batch=256):
     net.fit_standardiser(Xd.data_ptr(), Td.data_ptr(), ntrain)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = ws.train(net, Xd, Td, ntrain, steps=steps, batch=batch, lr=1e-3, seed=1004)
+    losses = ws.train(net, Xd, Td, ntrain, steps=steps, batch=batch, lr=lr, seed=1004, schedule="cos")
     t_train = time.perf_counter() - t0
     test = scen[ntrain:]
     stream = torch.cuda.Stream()
@@ -466,6 +466,7 @@ def learned_warm_start(args, ntrain=4096, ntest=512, steps=2000, batch=256):
     res["warm"]["timing"] = ("host wall clock of inference, scatter and sqp_solve_graph on a prepared handle, plus "
                              "the cold fallback (new handle) of instances that failed the convergence test")
     return {"train_scenarios": ntrain, "held_out": ntest, "net": dims, "train_steps": steps, "batch": batch,
+            "lr": f"{lr} with cosine decay to 0 (Adam)",
             "data_seconds": t_data, "train_seconds": t_train, "data_converged": int(conv.sum()),
             "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-10:].mean()),
             "cold": res["cold"], "warm": res["warm"],

@@ -76,9 +76,12 @@ def solve_targets(grids, opts, precision="mixed", chunk=256, base_rho=2e4):
     return T, conv, iters, objs
 
 
-def train(net, X_dev, T_dev, n: int, steps: int, batch: int, lr: float, seed: int, stream=None):
-    """Mini-batch Adam on rows [0, n) of the device data set; returns the
-    loss of every step (read back once at the end)."""
+def train(net, X_dev, T_dev, n: int, steps: int, batch: int, lr: float, seed: int, schedule: str = "const"):
+    """Mini-batch Adam on rows [0, n) of the device data set (shuffled every
+    epoch); schedule "cos" decays the learning rate from lr to 0 along half a
+    cosine.  Returns the loss of every step (read back once at the end)."""
+    import math
+
     import torch
 
     rng = np.random.default_rng(seed)
@@ -88,8 +91,8 @@ def train(net, X_dev, T_dev, n: int, steps: int, batch: int, lr: float, seed: in
     idx_all = torch.from_numpy(order).to(dev)
     for k in range(steps):
         idx = idx_all[k * batch:(k + 1) * batch]
-        net.train_step(X_dev.data_ptr(), T_dev.data_ptr(), idx.data_ptr(), batch, lr,
-                       losses.data_ptr() + 4 * k)
+        lk = lr if schedule == "const" else max(lr * 0.5 * (1.0 + math.cos(math.pi * k / steps)), 1e-7)
+        net.train_step(X_dev.data_ptr(), T_dev.data_ptr(), idx.data_ptr(), batch, lk, losses.data_ptr() + 4 * k)
     net.sync()
     return losses.cpu().numpy()
 
