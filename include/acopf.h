@@ -180,6 +180,22 @@ acopf_status admm_solve_qp(acopf_handle h, double delta, const admm_options* o);
  * device is synchronised first.  Returns when the solve is complete. */
 acopf_status sqp_solve_graph(acopf_handle h, const sqp_options* o, int32_t check_every);
 
+/* Linear feasibility projection (Sec. II, eq. linfeas; Alg. 1 line 3): the
+ * current iterate of every instance -- as last set by acopf_set_iterate or a
+ * warm start, or left by the last solve -- is replaced by the nearest point
+ * (Euclidean norm over [pg | qg | w | theta | wR | wI]) that satisfies the
+ * NLP's linear constraints: the bus power balances (eq. opfc5, opfc6, with the
+ * branch flows of eq. acopf_pf, linear in w, wR, wI), the bounds of pg, qg,
+ * w and theta (opfc1-4) and theta_ref = 0.  Solved in FP64 by component ADMM
+ * (generator box projections, a 4-variable box QP per branch over its wR, wI
+ * and copies of its end-bus voltages, closed-form bus updates) with penalty
+ * rho > 0 (0.5 suits unit-weight objectives) until the l_inf primal and dual
+ * residuals of every instance are <= eps, or max_iter iterations; iters and
+ * rs[2] (largest r and s) may be NULL.  The next sqp_solve starts from the
+ * projected point.  Allocates scratch for the call; synchronises the stream. */
+acopf_status acopf_project_linear(acopf_handle h, double rho, double eps, int32_t max_iter, int32_t* iters,
+                                  double* rs);
+
 /* Warm start of instance inst: x0 = NLP point in the layout of
  * acopf_set_iterate (may be NULL; pi is reset to 0), lambda0 = ADMM multipliers:
  * the lam array of acopf_admm_state (8 per branch) followed by its lg array

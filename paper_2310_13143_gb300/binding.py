@@ -126,6 +126,7 @@ def lib():
             "acopf_get_profile": (S, [H, DP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
             "acopf_set_warm_start_device": (S, [H, C.c_void_p, C.c_int64, C.c_double, S, S, S, S]),
             "sqp_solve_graph": (S, [H, C.POINTER(sqp_options), C.c_int32]),
+            "acopf_project_linear": (S, [H, C.c_double, C.c_double, C.c_int32, IP, DP]),
             "acopf_autotune": (S, [H, C.c_char_p, C.c_int32, IP, DP]),
             "acopf_mlp_create": (S, [IP, C.c_int32, C.c_int32, C.c_int32, C.POINTER(H)]),
             "acopf_mlp_destroy": (S, [H]),
@@ -157,7 +158,7 @@ EXPORTED = ["acopf_default_options", "admm_default_options", "sqp_default_option
             "acopf_set_iterate", "acopf_get_iterate", "acopf_build_qp", "acopf_get_qp", "acopf_get_admm_state",
             "acopf_set_admm_state", "admm_iterate", "acopf_get_step", "acopf_launch_count", "acopf_profile",
             "acopf_get_profile", "acopf_get_history", "admm_iterate_static", "acopf_get_profile_phases",
-            "acopf_tune", "acopf_set_warm_start_device", "sqp_solve_graph", "acopf_autotune", "acopf_mlp_create", "acopf_mlp_destroy",
+            "acopf_tune", "acopf_set_warm_start_device", "sqp_solve_graph", "acopf_autotune", "acopf_project_linear", "acopf_mlp_create", "acopf_mlp_destroy",
             "acopf_mlp_set_stream", "acopf_mlp_last_error", "acopf_mlp_num_params", "acopf_mlp_set_params",
             "acopf_mlp_get_params", "acopf_mlp_get_grads", "acopf_mlp_fit_standardiser",
             "acopf_mlp_get_standardiser", "acopf_mlp_forward", "acopf_mlp_train_step", "acopf_mlp_sync",
@@ -268,6 +269,14 @@ class Solver:
 
     def sqp_solve_graph(self, opts: sqp_options | None = None, check_every: int = 4):
         self._check(lib().sqp_solve_graph(self.h, C.byref(opts or default_sqp()), int(check_every)))
+
+    def project_linear(self, rho=0.5, eps=1e-6, max_iter=20000):
+        """Project every instance's iterate onto the linear constraints; returns
+        (iterations, largest primal residual, largest dual residual)."""
+        it = C.c_int32()
+        rs = np.zeros(2)
+        self._check(lib().acopf_project_linear(self.h, float(rho), float(eps), int(max_iter), C.byref(it), _dp(rs)))
+        return it.value, rs[0], rs[1]
 
     def autotune(self, cache_path: str | None = None, iters: int = 50):
         """Returns ((threads, ctas_per_sm, stages), us_per_iter or -1 if cached)."""

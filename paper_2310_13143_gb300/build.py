@@ -12,7 +12,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libacopf.so")
-SOURCES = ["api.cu", "sqp_kernels.cu", "sweep.cu", "mlp.cu"]
+SOURCES = ["api.cu", "sqp_kernels.cu", "sweep.cu", "mlp.cu", "linfeas.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

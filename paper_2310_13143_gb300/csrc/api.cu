@@ -1273,4 +1273,15 @@ acopf_status acopf_set_warm_start_device(acopf_handle h, const float* pred, int6
   return ACOPF_OK;
 }
 
+acopf_status acopf_project_linear(acopf_handle h, double rho, double eps, int32_t max_iter, int32_t* iters,
+                                  double* rs) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !(rho > 0) || !(eps > 0) || max_iter < 1)
+    return fail(c, ACOPF_EINVAL, "acopf_project_linear: rho > 0, eps > 0, max_iter >= 1 required");
+  acopf_status s = project_linear(*c, rho, eps, max_iter, 25, iters, rs);
+  if (s) return s;
+  c->warm_x = true;  // the next sqp_solve starts from the projected point
+  return ACOPF_OK;
+}
+
 }  // extern "C"

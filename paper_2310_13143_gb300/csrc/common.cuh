@@ -180,6 +180,7 @@ void launch_merit(Ctx& c);
 void launch_accept_and_kkt(Ctx& c);
 void launch_fill_rho(Ctx& c, double rho);
 void launch_commit_rho(Ctx& c);
+acopf_status project_linear(Ctx& c, double rho, double eps, int max_iter, int check, int* iters, double* rs);
 void launch_warm_scatter(Ctx& c, const float* pred, long long ld, int nb, int nl, int ng, double base_rho, int use_x,
                          int use_pi, int use_lam, int use_rho);
 

@@ -329,3 +329,29 @@ def test_mixed_sweep_launch_shapes_agree():
         for a, b in zip(ref, got):
             for key in ("x", "z", "lam", "xg", "zg", "lg", "zb", "nu", "ul"):
                 np.testing.assert_array_equal(a[key], b[key], err_msg=f"{bt}:{st}:{key}")
+
+
+@pytest.mark.parametrize("name", ["syn30", "syn30_shunt_tap", "syn118", "hub41", "two_bus"])
+def test_linear_projection_matches_oracle(name):
+    """acopf_project_linear (eq. linfeas) against the exact projection of the
+    oracle: every instance of a two-instance handle, from perturbed starts."""
+    from oracle import linfeas as olf
+
+    g = GRIDS[name]()
+    m = oracle.Model(g)
+    rng = np.random.default_rng(5)
+    starts = [_perturbed(m, rng, 0.05), _perturbed(m, rng, 0.2)]
+    s = binding.Solver([g, g], precision="fp64")
+    for k, x0 in enumerate(starts):
+        s.set_iterate(k, x0)
+    it, r, sres = s.project_linear(rho=0.5, eps=1e-10, max_iter=40000)
+    assert r <= 1e-10 and sres <= 1e-10, (it, r, sres)
+    E, e, lo, hi = olf.linear_constraints(m)
+    for k, x0 in enumerate(starts):
+        want, _ = olf.project(m, x0)
+        got, _ = s.get_iterate(k)
+        # the ADMM residual bound 1e-10 leaves the point within ~1e-8 of the projection
+        np.testing.assert_allclose(got, want, atol=2e-7)
+        assert np.max(np.abs(E @ got - e)) <= 1e-6
+        assert np.all(got >= lo - 1e-12) and np.all(got <= hi + 1e-12)
+    s.close()
