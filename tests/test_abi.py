@@ -88,3 +88,21 @@ def test_null_arguments(lib):
     assert lib.acopf_create(None, 1, None, C.byref(h)) == 1
     assert lib.acopf_destroy(None) == 1
     assert lib.sqp_solve(None, None) == 1
+
+
+def test_new_entry_points_validate_arguments_on_the_host(lib):
+    """The projection, graph solve, autotune, warm-start scatter and network
+    calls reject bad arguments before touching a device."""
+    EINVAL = 1
+    assert lib.acopf_project_linear(None, 0.5, 1e-6, 10, None, None) == EINVAL
+    assert lib.sqp_solve_graph(None, None, 1) == EINVAL
+    assert lib.acopf_autotune(None, None, 10, None, None) == EINVAL
+    assert lib.acopf_set_warm_start_device(None, None, 0, 2e4, 1, 1, 1, 1) == EINVAL
+    h = C.c_void_p()
+    bad_dims = (C.c_int32 * 3)(16, 12, 8)  # 12 is not a multiple of 8
+    assert lib.acopf_mlp_create(bad_dims, 2, 64, 0, C.byref(h)) == EINVAL
+    assert lib.acopf_mlp_create(None, 2, 64, 0, C.byref(h)) == EINVAL
+    ok_dims = (C.c_int32 * 3)(16, 32, 8)
+    assert lib.acopf_mlp_create(ok_dims, 2, 0, 0, C.byref(h)) == EINVAL
+    assert lib.acopf_gemm_bf16(None, None, None, 8, 8, 8, 1, None, None) == EINVAL
+    assert lib.acopf_mlp_train_step(None, None, None, None, 1, C.c_float(1e-3), None) == EINVAL
