@@ -436,40 +436,58 @@ __global__ void k_input(const float* X, const int* idx, int rows, int Mb, int d0
 }
 
 // mean squared error against standardised targets: dY = 2 (Y - T) / (rows * N)
-// in bfloat16 (row-major and transposed), per-block sums of squares
+// in bfloat16, row-major and transposed (32 x 32 tiles transposed through
+// shared memory so both stores coalesce), one sum of squares per block.
+// Grid (ceil(N / 32), Mb / 32), block 32 x 8.
 __global__ void k_mse(const float* Y, const float* T, const int* idx, int rows, int Mb, int N, const float* mu,
                       const float* sd, bf16* D, bf16* DT, double* part) {
+  __shared__ bf16 tile[32][34];
   __shared__ double red[256];
-  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.x * 32 + threadIdx.x;
+  const int r0 = blockIdx.y * 32;
   double sq = 0.0;
-  if (i < (size_t)Mb * N) {
-    int r = (int)(i / N), n = (int)(i % N);
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int r = r0 + k;
     float g = 0.0f;
-    if (r < rows) {
-      size_t src = idx ? (size_t)idx[r] : (size_t)r;
-      float t = (T[src * N + n] - mu[n]) / sd[n];
-      float d = Y[i] - t;
-      sq = (double)d * (double)d;
+    if (n < N && r < rows) {
+      const size_t src = idx ? (size_t)idx[r] : (size_t)r;
+      const float t = (T[src * N + n] - mu[n]) / sd[n];
+      const float d = Y[(size_t)r * N + n] - t;
+      sq += (double)d * (double)d;
       g = 2.0f * d / ((float)rows * (float)N);
     }
-    bf16 h = __float2bfloat16_rn(g);
-    D[i] = h;
-    DT[(size_t)n * Mb + r] = h;
+    const bf16 h = __float2bfloat16_rn(g);
+    if (n < N) D[(size_t)r * N + n] = h;
+    tile[k][threadIdx.x] = h;
   }
-  red[threadIdx.x] = sq;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int nn = blockIdx.x * 32 + k;
+    if (nn < N) DT[(size_t)nn * Mb + r0 + threadIdx.x] = tile[threadIdx.x][k];
+  }
+  const int t = threadIdx.y * 32 + threadIdx.x;
+  red[t] = sq;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (t < st) red[t] += red[t + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+  if (t == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
 }
 
+// sum of n partial sums in a fixed order (strided per thread, then a tree);
+// one block of 1024 threads
 __global__ void k_sum(const double* part, int n, double scale, float* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  __shared__ double red[1024];
   double s = 0.0;
-  for (int i = 0; i < n; ++i) s += part[i];
-  *out = (float)(s * scale);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = (float)(red[0] * scale);
 }
 
 // column sums of a bfloat16 matrix [rows x N] (bias gradients), fixed order
@@ -824,7 +842,7 @@ acopf_status acopf_mlp_create(const int32_t* dims, int32_t nlayers, int32_t max_
        dalloc(n, &n->sd_x, dims[0]) && dalloc(n, &n->mu_y, dims[nlayers]) && dalloc(n, &n->sd_y, dims[nlayers]) &&
        dalloc(n, &n->err, 1) && dalloc(n, &n->loss, 1);
   if (ok) {
-    n->nparts = (int)(((size_t)Mb * dims[nlayers] + 255) / 256);
+    n->nparts = (int)(((size_t)dims[nlayers] + 31) / 32 * ((size_t)Mb / 32));
     ok = dalloc(n, &n->part, n->nparts);
   }
   if (ok) {
@@ -988,10 +1006,10 @@ acopf_status acopf_mlp_train_step(acopf_mlp_handle h, const float* X, const floa
   NCK(cudaGetLastError());
   acopf_status s = forward(n, rows);
   if (s) return s;
-  size_t ty = (size_t)Mb * dn;
-  k_mse<<<(unsigned)((ty + 255) / 256), 256, 0, n->stream>>>(n->Y, T, idx, rows, Mb, dn, n->mu_y, n->sd_y, n->D[nl],
-                                                              n->DT[nl], n->part);
-  k_sum<<<1, 32, 0, n->stream>>>(n->part, n->nparts, 1.0 / ((double)rows * dn), n->loss);
+  dim3 mgrid((dn + 31) / 32, Mb / 32);
+  k_mse<<<mgrid, dim3(32, 8), 0, n->stream>>>(n->Y, T, idx, rows, Mb, dn, n->mu_y, n->sd_y, n->D[nl], n->DT[nl],
+                                              n->part);
+  k_sum<<<1, 1024, 0, n->stream>>>(n->part, (int)(mgrid.x * mgrid.y), 1.0 / ((double)rows * dn), n->loss);
   NCK(cudaGetLastError());
   for (int l = nl - 1; l >= 0; --l) {
     NCK(run_gemm(n->bwd_w[l], n->ws, n->err, n->stream, n->spin, n->sms));
