@@ -526,6 +526,43 @@ def gemm_roofline(M=8192, N=8192, K=8192, reps=5):
             "timing": "CUDA events around the kernel on its stream, mean of the repetitions, L2 flushed between them"}
 
 
+def mlp_train_steps(steps, warmup, batch=256, dims=(4000, 512, 512, 512, 46504), n=1024):
+    """Training steps of the warm-start network at the 2,000-bus sizes on
+    seeded random data (the solver is not involved): device time per step and
+    the step's matrix-product FLOP rate."""
+    import torch
+
+    from paper_2310_13143_gb300 import binding, gridgen
+
+    dims = list(dims)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    X = torch.randn(n, dims[0], device="cuda", generator=gen)
+    T = torch.randn(n, dims[-1], device="cuda", generator=gen)
+    net = binding.Mlp(dims, max_batch=batch)
+    stream = torch.cuda.Stream()
+    net.set_stream(stream.cuda_stream)
+    net.set_params(gridgen.mlp_init(dims, seed=7))
+    net.fit_standardiser(X.data_ptr(), T.data_ptr(), n)
+    idx = torch.arange(batch, dtype=torch.int32, device="cuda")
+    for _ in range(warmup):
+        net.train_step(X.data_ptr(), T.data_ptr(), idx.data_ptr(), batch, 1e-3, None)
+    net.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        net.train_step(X.data_ptr(), T.data_ptr(), idx.data_ptr(), batch, 1e-3, None)
+    b.record(stream)
+    net.sync()
+    ms = a.elapsed_time(b) / steps
+    # forward 2 M sum(in out); backward twice that (weight and input gradients; none for layer 0's input)
+    fwd = 2.0 * batch * sum(dims[i] * dims[i + 1] for i in range(len(dims) - 1))
+    bwd = 2.0 * fwd - 2.0 * batch * dims[0] * dims[1]
+    net.close()
+    return {"metric": "warm-start network training step", "value": ms, "unit": "ms/step", "steps": steps,
+            "warmup": warmup, "batch": batch, "net": dims, "gemm_tflops_per_step": (fwd + bwd) / 1e12,
+            "effective_tflop_s": (fwd + bwd) / (ms * 1e-3) / 1e12}
+
+
 def workload_grids(name):
     from paper_2310_13143_gb300 import gridgen
 
@@ -669,7 +706,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-rho-sweep", action="store_true")
     ap.add_argument("--no-large", action="store_true")
-    ap.add_argument("--workload", default="syn2000", choices=["syn2000", "batched", "syn70k", "syn70k_x16", "gemm"])
+    ap.add_argument("--workload", default="syn2000",
+                    choices=["syn2000", "batched", "syn70k", "syn70k_x16", "gemm", "mlp_train"])
     ap.add_argument("--gemm-shape", default="8192,8192,8192")
     ap.add_argument("--sweep-iters", type=int, default=0)
     args = ap.parse_args()
@@ -684,6 +722,13 @@ def main():
         import torch
 
         torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if args.workload == "mlp_train":  # the warm-start network's training step alone
+        from paper_2310_13143_gb300.build import build
+
+        build()
+        if rank == 0:
+            print(json.dumps(mlp_train_steps(args.steps, args.warmup)), flush=True)
+        return
     if args.workload == "gemm":  # the tensor-core product alone (profiling and roofline studies)
         from paper_2310_13143_gb300.build import build
 
