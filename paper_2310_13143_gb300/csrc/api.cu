@@ -1,4 +1,5 @@
-// Host implementation of the C ABI declared in include/acopf.h.
+// Host implementation of the C ABI declared in include/acopf.h (and of
+// acopf_set_warm_start_device from include/acopf_mlp.h).
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>

@@ -63,8 +63,6 @@ struct Epi {
   int M, N;             // output extent
   int rows_valid;       // bf16 outputs of rows >= rows_valid are written as 0
   const float* bias;    // [N] or null
-  const float* scale;   // [N] or null: EPI_F32 writes (acc + bias) * scale + shift
-  const float* shift;
   float* f32;           // FP32 row-major output (EPI_F32, EPI_PARTIAL; EPI_GELU: the pre-activation)
   int ld_f32;
   size_t split_stride;  // EPI_PARTIAL: elements between the partial tiles of consecutive K splits
@@ -156,9 +154,7 @@ __device__ __forceinline__ void epi_one(const Epi& e, int m, int n, float acc, i
   if (m >= e.M || n >= e.N) return;
   switch (e.op) {
     case EPI_F32: {
-      float v = acc + (e.bias ? e.bias[n] : 0.0f);
-      if (e.scale) v = v * e.scale[n] + e.shift[n];
-      e.f32[(size_t)m * e.ld_f32 + n] = v;
+      e.f32[(size_t)m * e.ld_f32 + n] = acc + (e.bias ? e.bias[n] : 0.0f);
       break;
     }
     case EPI_GELU: {
@@ -203,12 +199,7 @@ __device__ __forceinline__ void epi_store16(const Epi& e, int m, int n, const fl
       float w[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        float x = v[j];
-        if (e.op == EPI_F32) {
-          if (e.bias) x += e.bias[n + j];
-          if (e.scale) x = x * e.scale[n + j] + e.shift[n + j];
-        }
-        w[j] = x;
+        w[j] = v[j] + (e.op == EPI_F32 && e.bias ? e.bias[n + j] : 0.0f);
       }
       if (((uintptr_t)dst & 15) == 0) {
 #pragma unroll
