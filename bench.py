@@ -341,7 +341,7 @@ def rho_sweep(grid, precision, rhos=(2e3, 5e3, 1e4, 2e4, 5e4), reps=3):
 
 
 def batched_solve(grids, plain_sample=8):
-    """Config 3 solved to the end: every instance of the uneven batch in one
+    """The uneven 320-instance batch solved to the end: every instance in one
     handle (launch shape from the autotuner, SQP loop replayed from a CUDA
     graph), against a plain sample of the same instances solved one at a
     time, cold, in FP64."""
@@ -402,7 +402,7 @@ def batched_solve(grids, plain_sample=8):
 
 
 def learned_warm_start(args, ntrain=4096, ntest=512, steps=6000, batch=256, lr=3e-3):
-    """Config 4: the warm-start network trained on cold solves of sampled
+    """The learned warm start: the network trained on cold solves of sampled
     loads of the 2,000-bus grid and judged on held-out scenarios against
     cold starts of the same scenarios."""
     import numpy as np

@@ -39,6 +39,29 @@ ACOPF_HD inline T clampv(T v, T lo, T hi) {
   return v < lo ? lo : (v > hi ? hi : v);
 }
 
+// Quotient and reciprocal square root of the line and bus updates.  FP64
+// keeps the correctly rounded operations; the FP32 kernel takes the
+// special-function unit's approximations (__fdividef, rsqrtf: within a few
+// ulp), which shorten the dependent chain of each branch's solve.  The FP32
+// box QP refines its final solve with a residual in twice the precision, and
+// the ADMM tolerances of the FP32 path lie far above these errors.
+ACOPF_HD inline double div_w(double a, double b) { return a / b; }
+ACOPF_HD inline float div_w(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
+}
+ACOPF_HD inline double rsqrt_w(double a) { return 1.0 / sqrt(a); }
+ACOPF_HD inline float rsqrt_w(float a) {
+#ifdef __CUDA_ARCH__
+  return rsqrtf(a);
+#else
+  return 1.0f / sqrtf(a);
+#endif
+}
+
 // ----------------------------------------------------------- line update
 // min 1/2 x'Qx + c'x  s.t. lo <= x <= hi,  R_r x <= rb_r for the two
 // normalised line-limit rows that are on, and  alo <= x1 - x3 <= ahi  (the
@@ -86,23 +109,19 @@ ACOPF_HD inline bool chol4_masked(const T h[10], unsigned fr, const T r[4], T p[
   T a01 = f0 && f1 ? h[1] : T(0), a02 = f0 && f2 ? h[2] : T(0), a03 = f0 && f3 ? h[3] : T(0);
   T a12 = f1 && f2 ? h[5] : T(0), a13 = f1 && f3 ? h[6] : T(0), a23 = f2 && f3 ? h[8] : T(0);
   if (!(a00 > T(0))) return false;
-  T l00 = sqrt(a00);
-  T i00 = T(1) / l00;
+  T i00 = rsqrt_w(a00);
   T l10 = a01 * i00, l20 = a02 * i00, l30 = a03 * i00;
   T d1 = a11 - l10 * l10;
   if (!(d1 > T(0))) return false;
-  T l11 = sqrt(d1);
-  T i11 = T(1) / l11;
+  T i11 = rsqrt_w(d1);
   T l21 = (a12 - l20 * l10) * i11, l31 = (a13 - l30 * l10) * i11;
   T d2 = a22 - l20 * l20 - l21 * l21;
   if (!(d2 > T(0))) return false;
-  T l22 = sqrt(d2);
-  T i22 = T(1) / l22;
+  T i22 = rsqrt_w(d2);
   T l32 = (a23 - l30 * l20 - l31 * l21) * i22;
   T d3 = a33 - l30 * l30 - l31 * l31 - l32 * l32;
   if (!(d3 > T(0))) return false;
-  T l33 = sqrt(d3);
-  T i33 = T(1) / l33;
+  T i33 = rsqrt_w(d3);
   T y0 = r[0] * i00;
   T y1 = (r[1] - l10 * y0) * i11;
   T y2 = (r[2] - l20 * y0 - l21 * y1) * i22;
@@ -176,10 +195,10 @@ ACOPF_HD inline int box_qp(const T h[10], const T b[4], const T lo[4], const T h
       if ((fx >> i) & 1u) continue;
       T dx = y[i] - x[i];
       if (y[i] < lo[i] && dx < T(0)) {
-        T a = (lo[i] - x[i]) / dx;
+        T a = div_w(lo[i] - x[i], dx);
         if (a < alpha) { alpha = a; blk = i; side = -1; }
       } else if (y[i] > hi[i] && dx > T(0)) {
-        T a = (hi[i] - x[i]) / dx;
+        T a = div_w(hi[i] - x[i], dx);
         if (a < alpha) { alpha = a; blk = i; side = 1; }
       }
     }
@@ -319,7 +338,8 @@ ACOPF_HD inline void line_solve(const LineQP<T>& P, T x[4], T u[4], T beta, T al
       T hr = row_h(P, r, x);
       T un = u[r] + beta * hr;
       un = un > T(0) ? un : T(0);
-      T m = hr > -un / beta ? hr : -un / beta;
+      const T mb = div_w(-un, beta);
+      T m = hr > mb ? hr : mb;
       viol = fmax(viol, fabs(m));
       u[r] = un;
     }

@@ -162,8 +162,8 @@ __device__ __forceinline__ void gen_phase(const SweepP<T>& p, int g, float sc) {
   T rho = b.z;
   // eq. gen_kernel: clamp((rho z - lambda - f') / (f'' + rho)) and clamp((rho z - lambda) / rho)
   V2<T> x;
-  x.x = clampv((rho * z.x - lam.x - a.x) / (a.y + rho), a.z, a.w);
-  x.y = clampv((rho * z.y - lam.y) / rho, b.x, b.y);
+  x.x = clampv(div_w(rho * z.x - lam.x - a.x, a.y + rho), a.z, a.w);
+  x.y = clampv(div_w(rho * z.y - lam.y, rho), b.x, b.y);
   ((V2<T>*)d.XG)[g] = x;
 }
 
@@ -347,13 +347,13 @@ __device__ __forceinline__ void entry_load(const Dev& d, int c, V4<T>& x, V4<T>&
 // ends with - (they draw power from the bus)
 template <typename T>
 __device__ __forceinline__ void entry_sums(int c, const V4<T>& x, const V4<T>& lm, T r, T* S) {
-  S[0] += T(1) / r;
+  S[0] += div_w(T(1), r);
   if (c < 0) {
-    S[1] += (lm.x + r * x.x) / r;
-    S[2] += (lm.y + r * x.y) / r;
+    S[1] += div_w(lm.x + r * x.x, r);
+    S[2] += div_w(lm.y + r * x.y, r);
   } else {
-    S[1] -= (lm.x + r * x.x) / r;
-    S[2] -= (lm.y + r * x.y) / r;
+    S[1] -= div_w(lm.x + r * x.x, r);
+    S[2] -= div_w(lm.y + r * x.y, r);
     S[3] += r;
     S[4] += lm.z + r * x.z;
     S[5] += lm.w + r * x.w;
@@ -366,17 +366,17 @@ template <typename T>
 __device__ __forceinline__ void bus_solve(const Dev& d, int bus, V4<T> br, int isref, const T* S, T& n1, T& n2,
                                           T& dw, T& dth) {
   const T gsh = br.z, bsh = br.w;
-  const T iQw = S[3] > T(0) ? T(1) / S[3] : T(0);  // a bus without branch ends has no voltage copies
+  const T iQw = S[3] > T(0) ? div_w(T(1), S[3]) : T(0);  // a bus without branch ends has no voltage copies
   const T M11 = S[0] + gsh * gsh * iQw;
   const T M22 = S[0] + bsh * bsh * iQw;
   const T M12 = -gsh * bsh * iQw;
   const T v1 = S[1] - gsh * S[4] * iQw - br.x;
   const T v2 = S[2] + bsh * S[4] * iQw - br.y;
   const T det = M11 * M22 - M12 * M12;
-  n1 = (M22 * v1 - M12 * v2) / det;
-  n2 = (M11 * v2 - M12 * v1) / det;
+  n1 = div_w(M22 * v1 - M12 * v2, det);
+  n2 = div_w(M11 * v2 - M12 * v1, det);
   dw = (S[4] + gsh * n1 - bsh * n2) * iQw;
-  dth = (isref || !(S[3] > T(0))) ? T(0) : S[5] / S[3];
+  dth = (isref || !(S[3] > T(0))) ? T(0) : div_w(S[5], S[3]);
   V2<T> zb, nu;
   zb.x = dw; zb.y = dth;
   nu.x = n1; nu.y = n2;
@@ -391,8 +391,8 @@ __device__ __forceinline__ void entry_update(const Dev& d, int c, const V4<T>& x
   if (c < 0) {
     const int g = -c - 1;
     V2<T> zn, ln;
-    zn.x = (lm.x + r * x.x - n1) / r;
-    zn.y = (lm.y + r * x.y - n2) / r;
+    zn.x = div_w(lm.x + r * x.x - n1, r);
+    zn.y = div_w(lm.y + r * x.y - n2, r);
     sm = fmax(sm, r * fmax(fabs(zn.x - zo.x), fabs(zn.y - zo.y)));
     const T rx = x.x - zn.x, ry = x.y - zn.y;
     rm = fmax(rm, fmax(fabs(rx), fabs(ry)));
@@ -402,8 +402,8 @@ __device__ __forceinline__ void entry_update(const Dev& d, int c, const V4<T>& x
     ((V2<T>*)d.LG)[g] = ln;
   } else {
     V4<T> zn, ln;
-    zn.x = (lm.x + r * x.x + n1) / r;
-    zn.y = (lm.y + r * x.y + n2) / r;
+    zn.x = div_w(lm.x + r * x.x + n1, r);
+    zn.y = div_w(lm.y + r * x.y + n2, r);
     zn.z = dw;
     zn.w = dth;
     const T a1 = fmax(fabs(zn.x - zo.x), fabs(zn.y - zo.y));
