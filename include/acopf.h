@@ -156,6 +156,34 @@ acopf_status acopf_destroy(acopf_handle h);
 /* Stream (a cudaStream_t) on which all later work is queued; NULL = legacy default. */
 acopf_status acopf_set_stream(acopf_handle h, void* cuda_stream);
 
+/* Device memory from the caller's allocator (for example a framework's caching
+ * allocator, so that the solver's state counts against its pool).  The paper
+ * prescribes no memory management; this is plumbing around Algorithms 1-2.
+ *
+ * alloc(bytes, ctx) returns a block of at least bytes of device memory on the
+ * handle's device, 256-byte aligned, or NULL; release(ptr, ctx) returns a
+ * block that alloc gave.  Both are called on the calling thread, only from
+ * inside calls on this handle.  The call waits for the handle's stream, then
+ * moves every block the handle owns (its model, iterate and ADMM state, the
+ * QP's export arrays) into new blocks from alloc, copying their contents, and
+ * releases the old ones through the allocator that made them.  Every later
+ * device allocation of the handle (export arrays, the scratch of
+ * acopf_project_linear, the device copy used by acopf_set_warm_start_device)
+ * goes through alloc, and acopf_destroy returns the blocks through release.
+ * The library calls release only after waiting for the handle's stream, so
+ * the blocks are idle when they are returned.  alloc = release = NULL goes
+ * back to cudaMalloc / cudaFree, moving the memory back the same way.  A
+ * captured SQP graph (sqp_solve_graph) is dropped and captured again.  The
+ * scratch of admm_iterate_static is not the handle's and does not move.
+ *
+ * Errors: EINVAL for a NULL handle, for only one of alloc and release NULL,
+ * or when alloc returned a block that is not 256-byte aligned device memory
+ * of the handle's device (that block is released again); ENOMEM when alloc
+ * returned NULL.  On any error the handle keeps its memory and its previous
+ * allocator. */
+acopf_status acopf_set_allocator(acopf_handle h, void* (*alloc)(size_t bytes, void* ctx),
+                                 void (*release)(void* ptr, void* ctx), void* ctx);
+
 /* Replace the loads of instance inst (host arrays of its nbus). */
 acopf_status acopf_set_loads(acopf_handle h, int32_t inst, const double* pd, const double* qd);
 

@@ -85,6 +85,11 @@ class acopf_admm_state(C.Structure):
 _lib = None
 
 
+# device allocator callbacks of acopf_set_allocator: alloc(bytes, ctx) -> ptr, release(ptr, ctx)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
 def lib():
     """Load libacopf.so; raises if it has not been built."""
     global _lib
@@ -103,6 +108,7 @@ def lib():
             "acopf_create": (S, [C.POINTER(acopf_grid), C.c_int32, C.POINTER(acopf_options), C.POINTER(H)]),
             "acopf_destroy": (S, [H]),
             "acopf_set_stream": (S, [H, C.c_void_p]),
+            "acopf_set_allocator": (S, [H, ALLOC_FN, FREE_FN, C.c_void_p]),
             "acopf_set_loads": (S, [H, C.c_int32, DP, DP]),
             "sqp_solve": (S, [H, C.POINTER(sqp_options)]),
             "admm_solve_qp": (S, [H, C.c_double, C.POINTER(admm_options)]),
@@ -153,7 +159,8 @@ def lib():
 
 
 EXPORTED = ["acopf_default_options", "admm_default_options", "sqp_default_options", "acopf_status_string",
-            "acopf_last_error", "acopf_create", "acopf_destroy", "acopf_set_stream", "acopf_set_loads", "sqp_solve",
+            "acopf_last_error", "acopf_create", "acopf_destroy", "acopf_set_stream", "acopf_set_allocator",
+            "acopf_set_loads", "sqp_solve",
             "admm_solve_qp", "acopf_set_warm_start", "acopf_get_solution", "acopf_get_residuals",
             "acopf_set_iterate", "acopf_get_iterate", "acopf_build_qp", "acopf_get_qp", "acopf_get_admm_state",
             "acopf_set_admm_state", "admm_iterate", "acopf_get_step", "acopf_launch_count", "acopf_profile",
@@ -230,11 +237,14 @@ class Solver:
         self.h = h
         self._keep_arr = arr
         self.precision = precision
+        self.device = device
+        self._alloc_cbs = None
 
     def close(self):
         if getattr(self, "h", None):
             lib().acopf_destroy(self.h)
             self.h = None
+        self._alloc_cbs = None  # after destroy, which may still call them
 
     def __del__(self):
         try:
@@ -259,6 +269,28 @@ class Solver:
     # ------------------------------------------------------------ solver calls
     def set_stream(self, stream_ptr: int):
         self._check(lib().acopf_set_stream(self.h, C.c_void_p(stream_ptr)))
+
+    def set_allocator(self, alloc=None, free=None):
+        """Move the handle's device memory to alloc(nbytes) -> int / free(ptr)
+        and allocate through them from now on; no arguments: back to
+        cudaMalloc.  The callbacks stay referenced until close()."""
+        if (alloc is None) != (free is None):
+            raise ValueError("give both alloc and free, or neither")
+        if alloc is None:
+            cbs = (ALLOC_FN(), FREE_FN())  # NULL function pointers
+        else:
+            cbs = (ALLOC_FN(lambda n, ctx: alloc(n)), FREE_FN(lambda p, ctx: free(p)))
+        self._check(lib().acopf_set_allocator(self.h, cbs[0], cbs[1], None))
+        # the old callbacks were last used inside the call above
+        self._alloc_cbs = cbs if alloc is not None else None
+
+    def use_torch_allocator(self):
+        """Serve the handle's device memory from torch's caching allocator."""
+        import torch
+
+        dev = self.device
+        self.set_allocator(lambda n: torch.cuda.caching_allocator_alloc(n, device=dev),
+                           torch.cuda.caching_allocator_delete)
 
     def set_loads(self, inst, pd, qd):
         pd, qd = _f64(pd), _f64(qd)

@@ -37,16 +37,51 @@ static acopf_status fail(Ctx* c, acopf_status s, const std::string& msg) {
   return s;
 }
 
-template <typename P>
-static cudaError_t dalloc(Ctx* c, P** p, size_t count) {
-  size_t bytes = sizeof(P) * (count > 0 ? count : 1);
+namespace acopf {
+cudaError_t ctx_alloc(Ctx& c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (!c.ualloc) return cudaMalloc(p, bytes);
+  void* q = c.ualloc(bytes, c.uctx);
+  if (!q) return cudaErrorMemoryAllocation;
+  cudaPointerAttributes a{};
+  const bool ok = ((uintptr_t)q & 255) == 0 && cudaPointerGetAttributes(&a, q) == cudaSuccess &&
+                  (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == c.device;
+  if (!ok) {
+    cudaGetLastError();
+    c.ufree(q, c.uctx);
+    return cudaErrorInvalidValue;
+  }
+  *p = q;
+  return cudaSuccess;
+}
+
+void ctx_free(Ctx& c, void* p) {
+  if (!p) return;
+  if (c.ualloc) c.ufree(p, c.uctx);
+  else cudaFree(p);
+}
+}  // namespace acopf
+
+static void release_block(const Ctx::Block& b) {
+  if (b.release) b.release(b.p, b.rctx);
+  else cudaFree(b.p);
+}
+
+// a zeroed block owned by the handle; *slot (a field of the handle) points to it
+static cudaError_t dalloc_bytes(Ctx* c, void** slot, size_t bytes) {
+  if (c->nblocks >= (int)(sizeof(c->blocks) / sizeof(c->blocks[0]))) return cudaErrorInvalidValue;
   void* v = nullptr;
-  cudaError_t e = cudaMalloc(&v, bytes);
+  cudaError_t e = ctx_alloc(*c, &v, bytes);
   if (e != cudaSuccess) return e;
   cudaMemsetAsync(v, 0, bytes, c->stream);
-  if (c->nallocs < (int)(sizeof(c->allocs) / sizeof(c->allocs[0]))) c->allocs[c->nallocs++] = v;
-  *p = (P*)v;
+  c->blocks[c->nblocks++] = Ctx::Block{v, bytes, slot, c->ualloc ? c->ufree : nullptr, c->uctx};
+  *slot = v;
   return cudaSuccess;
+}
+
+template <typename P>
+static cudaError_t dalloc(Ctx* c, P** p, size_t count) {
+  return dalloc_bytes(c, (void**)p, sizeof(P) * (count > 0 ? count : 1));
 }
 
 template <typename P>
@@ -383,8 +418,7 @@ acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_o
   A(d.dpg, G); A(d.dqg, G); A(d.dw, B); A(d.dth, B); A(d.dwr, L); A(d.dwi, L); A(d.pi_new, 4 * (size_t)L);
   A(d.flow, 4 * (size_t)L); A(d.aR, 4 * (size_t)L); A(d.aI, 4 * (size_t)L); A(d.bR, L); A(d.bI, L);
   A(d.gd1, G); A(d.gd2, G); A(d.rho_l, L); A(d.rho_g, G);
-  unsigned char* raw = nullptr;
-#define AR(ptr, bytes) do { raw = nullptr; if (e == cudaSuccess) e = dalloc(c, &raw, (bytes)); ptr = raw; } while (0)
+#define AR(ptr, bytes) if (e == cudaSuccess) e = dalloc_bytes(c, &(ptr), (bytes))
   AR(d.lrec, T * 4 * kRecChunks * (size_t)L);
   AR(d.grec, T * 8 * (size_t)G);
   AR(d.brec, T * 4 * (size_t)B);
@@ -470,12 +504,9 @@ acopf_status acopf_destroy(acopf_handle h) {
   Ctx* c = (Ctx*)h;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  for (int k = 0; k < c->nallocs; ++k) cudaFree(c->allocs[k]);
+  for (int k = 0; k < c->nblocks; ++k) release_block(c->blocks[k]);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
-  if (c->d.xbr) cudaFree(c->d.xbr);
-  if (c->d.xgen) cudaFree(c->d.xgen);
-  if (c->d.xbus) cudaFree(c->d.xbus);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph) cudaGraphDestroy(c->graph);
   if (c->h_running) cudaFreeHost(c->h_running);
@@ -488,6 +519,53 @@ acopf_status acopf_destroy(acopf_handle h) {
 acopf_status acopf_set_stream(acopf_handle h, void* s) {
   if (!h) return ACOPF_EINVAL;
   ((Ctx*)h)->stream = (cudaStream_t)s;
+  return ACOPF_OK;
+}
+
+acopf_status acopf_set_allocator(acopf_handle h, void* (*alloc)(size_t bytes, void* ctx),
+                                 void (*release)(void* ptr, void* ctx), void* ctx) {
+  Ctx* c = (Ctx*)h;
+  if (!c) return ACOPF_EINVAL;
+  if ((alloc == nullptr) != (release == nullptr))
+    return fail(c, ACOPF_EINVAL, "acopf_set_allocator: alloc and free must both be given or both be NULL");
+  CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+  drop_graph(c);
+  void* (*old_alloc)(size_t, void*) = c->ualloc;
+  void (*old_free)(void*, void*) = c->ufree;
+  void* old_ctx = c->uctx;
+  c->ualloc = alloc;
+  c->ufree = release;
+  c->uctx = ctx;
+  // new blocks first: on any failure the handle keeps its memory and allocator
+  std::vector<void*> fresh((size_t)c->nblocks, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < c->nblocks && e == cudaSuccess; ++k) e = ctx_alloc(*c, &fresh[k], c->blocks[k].bytes);
+  for (int k = 0; k < c->nblocks && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync(fresh[k], c->blocks[k].p, c->blocks[k].bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    for (void* p : fresh) ctx_free(*c, p);
+    c->ualloc = old_alloc;
+    c->ufree = old_free;
+    c->uctx = old_ctx;
+    const acopf_status s = e == cudaErrorMemoryAllocation ? ACOPF_ENOMEM
+                           : e == cudaErrorInvalidValue   ? ACOPF_EINVAL
+                                                          : ACOPF_ECUDA;
+    return fail(c, s,
+                std::string("acopf_set_allocator: moving the handle's memory failed: ") +
+                    (s == ACOPF_EINVAL ? "a block was not 256-byte aligned device memory of the handle's device"
+                                       : cudaGetErrorString(e)));
+  }
+  for (int k = 0; k < c->nblocks; ++k) {
+    Ctx::Block& b = c->blocks[k];
+    release_block(b);
+    b.p = fresh[k];
+    *b.slot = fresh[k];
+    b.release = alloc ? release : nullptr;
+    b.rctx = ctx;
+  }
   return ACOPF_OK;
 }
 
@@ -923,9 +1001,9 @@ acopf_status acopf_build_qp(acopf_handle h, double delta, double rho, int32_t us
   if (!c || !(delta > 0) || !(rho > 0)) return fail(c, ACOPF_EINVAL, "acopf_build_qp: bad arguments");
   Dev& d = c->d;
   if (!d.xbr) {
-    CK(cudaMalloc(&d.xbr, sizeof(double) * 110 * (size_t)(d.L > 0 ? d.L : 1)));
-    CK(cudaMalloc(&d.xgen, sizeof(double) * 6 * (size_t)d.G));
-    CK(cudaMalloc(&d.xbus, sizeof(double) * 2 * (size_t)d.B));
+    CK(dalloc(c, &d.xbr, 110 * (size_t)d.L));
+    CK(dalloc(c, &d.xgen, 6 * (size_t)d.G));
+    CK(dalloc(c, &d.xbus, 2 * (size_t)d.B));
   }
   sqp_options o;
   sqp_default_options(&o);

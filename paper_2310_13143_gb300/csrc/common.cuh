@@ -148,8 +148,21 @@ struct Ctx {
   int* h_gen_off = nullptr;
   int* h_gen_perm = nullptr;   // internal index -> user index (global)
   int* h_gen_iperm = nullptr;  // user index -> internal index
-  void* allocs[192];
-  int nallocs = 0;
+  // every device block the handle owns, with the handle field that points to
+  // it and the release function of the allocator that made it (null: cudaFree)
+  struct Block {
+    void* p;
+    size_t bytes;
+    void** slot;
+    void (*release)(void*, void*);
+    void* rctx;
+  };
+  Block blocks[192];
+  int nblocks = 0;
+  // the caller's device allocator (acopf_set_allocator); null: cudaMalloc / cudaFree
+  void* (*ualloc)(size_t, void*) = nullptr;
+  void (*ufree)(void*, void*) = nullptr;
+  void* uctx = nullptr;
   // sweep timing (acopf_profile)
   bool profiling = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -183,6 +196,12 @@ void launch_commit_rho(Ctx& c);
 acopf_status project_linear(Ctx& c, double rho, double eps, int max_iter, int check, int* iters, double* rs);
 void launch_warm_scatter(Ctx& c, const float* pred, long long ld, int nb, int nl, int ng, double base_rho, int use_x,
                          int use_pi, int use_lam, int use_rho);
+
+// device memory through the handle's allocator (cudaMalloc unless the caller
+// set one); ctx_alloc fails on a block that is not 256-byte aligned device
+// memory of the handle's device
+cudaError_t ctx_alloc(Ctx& c, void** p, size_t bytes);
+void ctx_free(Ctx& c, void* p);
 
 inline unsigned nblk(long n, int t) { return (unsigned)((n + t - 1) / t); }
 

@@ -217,8 +217,8 @@ __global__ void k_lf_finish(Dev d, LfState s) {
 }
 
 template <typename P>
-static cudaError_t lf_alloc(P** p, size_t n) {
-  return cudaMalloc((void**)p, sizeof(P) * (n > 0 ? n : 1));
+static cudaError_t lf_alloc(Ctx& c, P** p, size_t n) {
+  return ctx_alloc(c, (void**)p, sizeof(P) * (n > 0 ? n : 1));
 }
 
 acopf_status project_linear(Ctx& c, double rho, double eps, int max_iter, int check, int* iters, double* rs) {
@@ -226,13 +226,13 @@ acopf_status project_linear(Ctx& c, double rho, double eps, int max_iter, int ch
   LfState s;
   std::vector<void*> mem;
   cudaError_t e = cudaSuccess;
-#define LA(ptr, n) if (e == cudaSuccess) { e = lf_alloc(&(ptr), (n)); if (e == cudaSuccess) mem.push_back((void*)(ptr)); }
+#define LA(ptr, n) if (e == cudaSuccess) { e = lf_alloc(c, &(ptr), (n)); if (e == cudaSuccess) mem.push_back((void*)(ptr)); }
   LA(s.X, 2 * (size_t)d.L); LA(s.Z, 2 * (size_t)d.L); LA(s.LAM, 2 * (size_t)d.L);
   LA(s.XG, d.G); LA(s.ZG, d.G); LA(s.LG, d.G); LA(s.own, d.L); LA(s.WB, d.B);
   LA(s.x0, 2 * (size_t)d.G + d.B + 2 * (size_t)d.L); LA(s.res, 2 * (size_t)d.K);
 #undef LA
   auto release = [&]() {
-    for (void* p : mem) cudaFree(p);
+    for (void* p : mem) ctx_free(c, p);
   };
   if (e != cudaSuccess) {
     release();

@@ -98,6 +98,7 @@ def test_new_entry_points_validate_arguments_on_the_host(lib):
     assert lib.sqp_solve_graph(None, None, 1) == EINVAL
     assert lib.acopf_autotune(None, None, 10, None, None) == EINVAL
     assert lib.acopf_set_warm_start_device(None, None, 0, 2e4, 1, 1, 1, 1) == EINVAL
+    assert lib.acopf_set_allocator(None, binding.ALLOC_FN(), binding.FREE_FN(), None) == EINVAL
     h = C.c_void_p()
     bad_dims = (C.c_int32 * 3)(16, 12, 8)  # 12 is not a multiple of 8
     assert lib.acopf_mlp_create(bad_dims, 2, 64, 0, C.byref(h)) == EINVAL
