@@ -122,6 +122,8 @@ def measure(args, grid, precision, steps, warmup, local_rank, world, dev, with_e
     s.set_stream(stream.cuda_stream)
     opts = solver_options(binding, precision)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    # launch shape of the sweep from the autotuner (cached per device, precision and size class)
+    shape, tune_us = s.autotune(os.path.join(tempfile.gettempdir(), "acopf_tune_cache.json"), iters=200)
 
     for _ in range(warmup):
         s.sqp_solve(opts)
@@ -160,7 +162,9 @@ def measure(args, grid, precision, steps, warmup, local_rank, world, dev, with_e
     s.profile(False)
     sol = s.get_solution(0)
     out = dict(total_s=total_s, conv=conv, admm_iters=admm_iters, prof=prof, launches=launches, last=last,
-               obj=sol["obj"], clocks=clk.summary() if clk else None)
+               obj=sol["obj"], clocks=clk.summary() if clk else None,
+               launch_shape={"block_threads": shape[0], "ctas_per_sm": shape[1], "stages": shape[2],
+                             "tuned_us_per_iter": tune_us})
     if with_e2e:
         # end to end through the C ABI with host buffers: new loads in from
         # pinned host memory, solve, solution out
@@ -277,6 +281,7 @@ def run_gpu(args, rank, world, local_rank):
                      "bytes_per_iter": bpi, "iters_per_launch": iters_per_launch, "avg_launch_ms": avg_ms},
         "gpu_launches": m["launches"],
         "clocks": m["clocks"],
+        "launch_shape": m["launch_shape"],
     }
     if "e2e_s" in m:
         out["e2e"] = {"value": m["e2e_conv"] / m["e2e_s"] if m["e2e_s"] > 0 else 0.0, "unit": "solves/s",
@@ -611,6 +616,7 @@ def sweep_only(grids, precision, iters, launches, warmup, workload=None):
     s = binding.Solver(grids, precision=precision)
     stream = torch.cuda.Stream()
     s.set_stream(stream.cuda_stream)
+    shape, _ = s.autotune(os.path.join(tempfile.gettempdir(), "acopf_tune_cache.json"), iters=30)
     s.build_qp(1.0, 2e4, True)
     opts = binding.default_admm()
     for _ in range(warmup):
@@ -629,6 +635,7 @@ def sweep_only(grids, precision, iters, launches, warmup, workload=None):
     gbs = bpi / (us * 1e-6) / 1e9
     return {"instances": len(grids), "buses": B, "branches": L, "generators": G, "precision": precision,
             "us_per_iter": us, "admm_iter_per_s": 1e6 / us, "instance_iters_per_s": len(grids) * 1e6 / us,
+            "launch_shape": {"block_threads": shape[0], "ctas_per_sm": shape[1], "stages": shape[2]},
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                          "traffic": measured_traffic(workload, iters) if precision == "mixed" and workload else None,
                          "traffic_unit": "bytes per launch", "iters_per_launch": iters,

@@ -72,12 +72,15 @@ def test_state_moves_into_the_callers_allocator_and_back():
     live = a.bytes
     s.project_linear(rho=0.5, eps=1e-6, max_iter=200)
     assert a.calls > before and a.bytes == live
-    # graph replay after the move captures the new addresses
+    # graph replay after the move captures the new addresses (from the flat start again)
+    s.set_iterate(0, x0)
     s.sqp_solve_graph(_opts(), check_every=2)
     assert s.get_residuals(0)["result_name"] == "converged"
+    np.testing.assert_allclose(s.get_solution(0)["obj"], want_sol["obj"], rtol=1e-6)
     # back to cudaMalloc: everything returned
     s.set_allocator()
     assert a.bytes == 0
+    s.set_iterate(0, x0)
     sol2, _ = _solve(s, _opts())
     np.testing.assert_allclose(sol2["obj"], want_sol["obj"], rtol=1e-12)
     # and destroy releases through the allocator in force
