@@ -303,6 +303,42 @@ __device__ __forceinline__ void res_max2(unsigned long long* slots, int K, int s
   }
 }
 
+// res_max2 for two tasks at once
+template <typename T>
+__device__ __forceinline__ void res_max2_pair(unsigned long long* slots, int K, int slot, T ra, T sa, int ka, T rb,
+                                              T sb, int kb) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T ra2 = __shfl_down_sync(FULL, ra, o);
+    T sa2 = __shfl_down_sync(FULL, sa, o);
+    int ka2 = __shfl_down_sync(FULL, ka, o);
+    T rb2 = __shfl_down_sync(FULL, rb, o);
+    T sb2 = __shfl_down_sync(FULL, sb, o);
+    int kb2 = __shfl_down_sync(FULL, kb, o);
+    if (lane + o < 32 && ka2 == ka) {
+      ra = fmax(ra, ra2);
+      sa = fmax(sa, sa2);
+    }
+    if (lane + o < 32 && kb2 == kb) {
+      rb = fmax(rb, rb2);
+      sb = fmax(sb, sb2);
+    }
+  }
+  const int kpa = __shfl_up_sync(FULL, ka, 1), kpb = __shfl_up_sync(FULL, kb, 1);
+  if ((lane == 0 || kpa != ka) && ka >= 0) {
+    double rd = (double)ra, sd = (double)sa;
+    if (rd > 0.0) atomicMax(&slots[(slot * 2 + 0) * K + ka], (unsigned long long)__double_as_longlong(rd));
+    if (sd > 0.0) atomicMax(&slots[(slot * 2 + 1) * K + ka], (unsigned long long)__double_as_longlong(sd));
+  }
+  if ((lane == 0 || kpb != kb) && kb >= 0) {
+    double rd = (double)rb, sd = (double)sb;
+    if (rd > 0.0) atomicMax(&slots[(slot * 2 + 0) * K + kb], (unsigned long long)__double_as_longlong(rd));
+    if (sd > 0.0) atomicMax(&slots[(slot * 2 + 1) * K + kb], (unsigned long long)__double_as_longlong(sd));
+  }
+}
+
 // ---------------------------------------------------------- bus update
 // Bus update (eq. bus_kernel), multiplier update (eq. multiplier) and
 // residuals, one warp per task of consecutive whole buses: lane j takes one
@@ -439,6 +475,32 @@ __device__ __forceinline__ void seg_scan(int bus, T* S) {
   }
 }
 
+// seg_scan over two independent tasks at once (their shuffles interleave)
+template <typename T>
+__device__ __forceinline__ void seg_scan2(int bus_a, T* Sa, int bus_b, T* Sb) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T a[6], b[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      a[k] = __shfl_up_sync(FULL, Sa[k], o);
+      b[k] = __shfl_up_sync(FULL, Sb[k], o);
+    }
+    const int ua = __shfl_up_sync(FULL, bus_a, o);
+    const int ub = __shfl_up_sync(FULL, bus_b, o);
+    if (lane >= o && ua == bus_a) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) Sa[k] += a[k];
+    }
+    if (lane >= o && ub == bus_b) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) Sb[k] += b[k];
+    }
+  }
+}
+
 // the loads of one task of at most 32 entries: this lane's coupling, and for
 // the last lane of each bus its load and shunts (issued before any is used)
 template <typename T>
@@ -470,31 +532,43 @@ __device__ __forceinline__ TaskData<T> task_load(const Dev& d, Slot s, const int
   return a;
 }
 
-// one task of at most 32 entries from its loaded data; all 32 lanes call it
+// two tasks from their loaded data, solved together: the dependent chains of
+// the two (scan, 2x2 solve, broadcast, update, residual reduction) interleave
+// in one warp.  Tasks never share an entry or a bus, so the order of their
+// stores does not matter.  All 32 lanes call it.
 template <typename T>
-__device__ __forceinline__ void bus_task(const Dev& d, const TaskData<T>& a, int slot) {
+__device__ __forceinline__ void bus_task_pair(const Dev& d, const TaskData<T>& a, const TaskData<T>& b, int slot) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int bus = a.s.bus;
-  T S[6] = {0, 0, 0, 0, 0, 0};
-  if (bus >= 0) entry_sums(a.s.code, a.x, a.lm, a.r, S);
-  seg_scan(bus, S);
-  T n1 = 0, n2 = 0, dw = 0, dth = 0;
-  if (a.last) bus_solve(d, bus, a.br, a.isref, S, n1, n2, dw, dth);
-  const unsigned after = __ballot_sync(FULL, a.last) >> lane;
-  const int src = after ? lane + __ffs(after) - 1 : lane;
-  n1 = __shfl_sync(FULL, n1, src);
-  n2 = __shfl_sync(FULL, n2, src);
-  dw = __shfl_sync(FULL, dw, src);
-  dth = __shfl_sync(FULL, dth, src);
-  T rm = T(0), sm = T(0);
-  if (bus >= 0) {
-    entry_update(d, a.s.code, a.x, a.lm, a.zo, a.r, n1, n2, dw, dth, rm, sm);
-    // a NaN must not pass the residual test
-    if (!(rm == rm)) rm = T(1e30);
-    if (!(sm == sm)) sm = T(1e30);
+  T Sa[6] = {0, 0, 0, 0, 0, 0}, Sb[6] = {0, 0, 0, 0, 0, 0};
+  if (a.s.bus >= 0) entry_sums(a.s.code, a.x, a.lm, a.r, Sa);
+  if (b.s.bus >= 0) entry_sums(b.s.code, b.x, b.lm, b.r, Sb);
+  seg_scan2(a.s.bus, Sa, b.s.bus, Sb);
+  T n1a = 0, n2a = 0, dwa = 0, dta = 0, n1b = 0, n2b = 0, dwb = 0, dtb = 0;
+  if (a.last) bus_solve(d, a.s.bus, a.br, a.isref, Sa, n1a, n2a, dwa, dta);
+  if (b.last) bus_solve(d, b.s.bus, b.br, b.isref, Sb, n1b, n2b, dwb, dtb);
+  const unsigned ha = __ballot_sync(FULL, a.last) >> lane, hb = __ballot_sync(FULL, b.last) >> lane;
+  const int srca = ha ? lane + __ffs(ha) - 1 : lane, srcb = hb ? lane + __ffs(hb) - 1 : lane;
+  n1a = __shfl_sync(FULL, n1a, srca);
+  n1b = __shfl_sync(FULL, n1b, srcb);
+  n2a = __shfl_sync(FULL, n2a, srca);
+  n2b = __shfl_sync(FULL, n2b, srcb);
+  dwa = __shfl_sync(FULL, dwa, srca);
+  dwb = __shfl_sync(FULL, dwb, srcb);
+  dta = __shfl_sync(FULL, dta, srca);
+  dtb = __shfl_sync(FULL, dtb, srcb);
+  T rma = T(0), sma = T(0), rmb = T(0), smb = T(0);
+  if (a.s.bus >= 0) {
+    entry_update(d, a.s.code, a.x, a.lm, a.zo, a.r, n1a, n2a, dwa, dta, rma, sma);
+    if (!(rma == rma)) rma = T(1e30);
+    if (!(sma == sma)) sma = T(1e30);
   }
-  res_max2(d.res_slots, d.K, slot, rm, sm, a.s.inst);
+  if (b.s.bus >= 0) {
+    entry_update(d, b.s.code, b.x, b.lm, b.zo, b.r, n1b, n2b, dwb, dtb, rmb, smb);
+    if (!(rmb == rmb)) rmb = T(1e30);
+    if (!(smb == smb)) smb = T(1e30);
+  }
+  res_max2_pair(d.res_slots, d.K, slot, rma, sma, a.s.inst, rmb, smb, b.s.inst);
 }
 
 // one bus with more than 32 entries (entries [q0, q1) of ent); lanes loop
@@ -648,22 +722,24 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sweep(SweepP<T>
     if (prof) { tp1 = gtimer(); atomicAdd(&d.phase_ns[0], tp1 - tp0); }
     if (!grid_barrier(d.bar, d.err, p.spin_limit)) { aborted = true; break; }
     if (prof) { tp0 = gtimer(); atomicAdd(&d.phase_ns[1], tp0 - tp1); }
-    // phase B: buses, one warp task (consecutive whole buses) at a time in a
-    // two-deep pipeline: while task t is solved, the couplings of task t + 1
-    // and the slots of task t + 2 are in flight (every entry belongs to one
-    // task, so the loads ahead never read what the current task writes);
-    // loop bounds are uniform per warp so that all lanes reduce together
+    // phase B: buses, in warp tasks of consecutive whole buses, two tasks at a
+    // time (every entry belongs to one task, so the loads ahead never read
+    // what the current tasks write); loop bounds are uniform per warp so that
+    // all lanes reduce together
     {
       const int lane = threadIdx.x & 31, wid = tid >> 5, nw = nthreads >> 5;
       const Slot none = {-1, 0, -1};
-      Slot s1 = wid + nw < d.NT ? load_slot(d, wid + nw, lane) : none;
-      TaskData<T> cur = task_load<T>(d, wid < d.NT ? load_slot(d, wid, lane) : none, s_done);
-      for (int t = wid; t < d.NT; t += nw) {
-        const Slot s2 = t + 2 * nw < d.NT ? load_slot(d, t + 2 * nw, lane) : none;
-        const TaskData<T> nxt = task_load<T>(d, s1, s_done);
-        bus_task(d, cur, slot);
-        cur = nxt;
-        s1 = s2;
+      auto slot_at = [&](int t) { return t < d.NT ? load_slot(d, t, lane) : none; };
+      // tasks wid, wid + nw, ... taken two at a time; the slots of the next
+      // pair are in flight while a pair is solved
+      Slot s1a = slot_at(wid + 2 * nw), s1b = slot_at(wid + 3 * nw);
+      TaskData<T> ca = task_load<T>(d, slot_at(wid), s_done), cb = task_load<T>(d, slot_at(wid + nw), s_done);
+      for (int t = wid; t < d.NT; t += 2 * nw) {
+        bus_task_pair(d, ca, cb, slot);
+        ca = task_load<T>(d, s1a, s_done);
+        cb = task_load<T>(d, s1b, s_done);
+        s1a = slot_at(t + 4 * nw);
+        s1b = slot_at(t + 5 * nw);
       }
       for (int b = wid; b < d.NBIG; b += nw) bus_task_big(p, d.big[2 * b], d.big[2 * b + 1], slot, s_done);
     }
