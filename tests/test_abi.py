@@ -107,3 +107,14 @@ def test_new_entry_points_validate_arguments_on_the_host(lib):
     assert lib.acopf_mlp_create(ok_dims, 2, 0, 0, C.byref(h)) == EINVAL
     assert lib.acopf_gemm_bf16(None, None, None, 8, 8, 8, 1, None, None) == EINVAL
     assert lib.acopf_mlp_train_step(None, None, None, None, 1, C.c_float(1e-3), None) == EINVAL
+
+
+def test_allocator_binding_wants_both_callbacks():
+    """Solver.set_allocator refuses one callback without the other before
+    calling into the library."""
+    s = binding.Solver.__new__(binding.Solver)
+    s.h = None
+    with pytest.raises(ValueError):
+        s.set_allocator(alloc=lambda n: 0)
+    with pytest.raises(ValueError):
+        s.set_allocator(free=lambda p: None)
