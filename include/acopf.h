@@ -191,7 +191,7 @@ acopf_status acopf_set_loads(acopf_handle h, int32_t inst, const double* pd, con
  * every instance until each one converges or stops. */
 acopf_status sqp_solve(acopf_handle h, const sqp_options* o);
 
-/* One QP at the current iterate: build it (Alg. 1 line 6) and solve it by
+/* One QP at the current iterate: build it (Alg. 1, eq. QPsub) and solve it by
  * ADMM (Alg. 2); the step and the new multipliers become available through
  * acopf_get_step.  The iterate itself is not changed. */
 acopf_status admm_solve_qp(acopf_handle h, double delta, const admm_options* o);
@@ -199,7 +199,7 @@ acopf_status admm_solve_qp(acopf_handle h, double delta, const admm_options* o);
 /* sqp_solve with the SQP loop replayed from a CUDA graph: the first iteration
  * runs as individual launches (its ADMM start depends on the warm start); one
  * later iteration -- QP build, ADMM reset, the persistent sweep, step, merit
- * test and trust-region update (Alg. 1 lines 5-14, Alg. 2) -- is captured once
+ * test and trust-region update (the loop of Alg. 1, with Alg. 2) -- is captured once
  * per handle and option set and replayed until every instance has stopped.
  * The host reads the number of running instances from pinned memory after
  * every check_every >= 1 replays; replays after the last instance stopped
@@ -208,7 +208,7 @@ acopf_status admm_solve_qp(acopf_handle h, double delta, const admm_options* o);
  * device is synchronised first.  Returns when the solve is complete. */
 acopf_status sqp_solve_graph(acopf_handle h, const sqp_options* o, int32_t check_every);
 
-/* Linear feasibility projection (Sec. II, eq. linfeas; Alg. 1 line 3): the
+/* Linear feasibility projection (Sec. II, eq. linfeas; the initial feasibility step of Alg. 1): the
  * current iterate of every instance -- as last set by acopf_set_iterate or a
  * warm start, or left by the last solve -- is replaced by the nearest point
  * (Euclidean norm over [pg | qg | w | theta | wR | wI]) that satisfies the

@@ -114,7 +114,7 @@ int og_n_vars(const og_model* m) { return m->nvar; }
 
 void og_admittance(const og_model* m, double* Y) { memcpy(Y, m->Y, sizeof(double) * 8 * m->g.nbranch); }
 
-/* flat start (Alg. 1 line 1): w = 1, theta = 0, wR = 1, wI = 0, generators mid-box */
+/* flat start (the starting point of Alg. 1): w = 1, theta = 0, wR = 1, wI = 0, generators mid-box */
 void og_flat_start(const og_model* m, double* x) {
   const og_grid* g = &m->g;
   for (int k = 0; k < g->ngen; ++k) {

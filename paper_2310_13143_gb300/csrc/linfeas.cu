@@ -1,4 +1,4 @@
-// Linear feasibility projection (Sec. II, eq. linfeas; Alg. 1 line 3): the
+// Linear feasibility projection (Sec. II, eq. linfeas; the initial feasibility step of Alg. 1): the
 // current iterate x0 of every instance is replaced by the nearest point, in
 // the Euclidean norm, that satisfies the NLP's linear constraints -- the bus
 // power balances (eq. opfc5, opfc6 with the flows of eq. acopf_pf, linear in

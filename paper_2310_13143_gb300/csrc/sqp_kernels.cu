@@ -1,4 +1,4 @@
-// SQP-side kernels (FP64): model set-up, QP build (Alg. 1 line 6), step and
+// SQP-side kernels (FP64): model set-up, QP build (Alg. 1, eq. QPsub), step and
 // multiplier recovery after the ADMM sweep, l1 merit test with the trust-region
 // update (Sec. II-C/D), and the KKT measures used for termination.
 //
@@ -132,7 +132,7 @@ __global__ void k_admittance(int L, const double* r, const double* x, const doub
   Y[7 * L + l] = ys_im + 0.5 * bc[l];
 }
 
-// flat start (Alg. 1 line 1)
+// flat start (the starting point of Alg. 1)
 __global__ void k_flat_start(Dev d) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < d.G) {
@@ -652,7 +652,7 @@ __device__ void seg_reduce(const double* t, int n, int beg, int end, const int* 
   __syncthreads();
 }
 
-// l1 merit acceptance (Sec. II-C) and trust-region update (Alg. 1 lines 8-14)
+// l1 merit acceptance (Sec. II-C) and trust-region update (Alg. 1, acceptance and radius rules)
 __global__ void __launch_bounds__(256) k_decide(Dev d) {
   int k = blockIdx.x;
   InstCtl& c = d.ctl[k];

@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 CPU oracle, through the C ABI, on the same seeded inputs.
 
-* QP build (Alg. 1 line 6): every field, element by element, FP64.
+* QP build (Alg. 1, eq. QPsub): every field, element by element, FP64.
 * One ADMM iteration (Alg. 2) from the same random state: every coupling.
   The GPU solves each line subproblem by its augmented Lagrangian to 1e-11;
   the oracle solves it exactly, so the FP64 tolerance is 1e-7 relative to the

@@ -101,7 +101,7 @@ def test_two_bus_lossless_flow_closed_form():
 
 
 # --------------------------------------------------------------------------
-# QP build (Alg. 1 line 6): Hessian, elimination, flow maps, boxes
+# QP build (Alg. 1, eq. QPsub): Hessian, elimination, flow maps, boxes
 # --------------------------------------------------------------------------
 def _lagrangian_ij(m, x, pi, l):
     c4, _ = m.constraints(x)
