@@ -577,6 +577,52 @@ def test_sqp_multipliers_are_marginal_costs():
     assert p < 1e-7 and dd < 1e-6
 
 
+def test_recovered_line_multipliers_satisfy_stationarity():
+    """pi recovery (Sec. IV-B): at a tight 30-bus optimum, the Lagrangian
+    f + sum pi c + sum nu bal must be stationary in every branch's wR and wI
+    (free variables, no bounds).  The derivatives are central differences of
+    the model's constraint values, not the oracle's Jacobians, so an error in
+    those Jacobians cannot cancel between the recovery and the check.  All
+    four multipliers of a branch enter (one branch has both limits binding);
+    flipping the sign of any column breaks the identity by orders of
+    magnitude."""
+    g = gg.grid_30bus()
+    m = oracle.Model(g)
+    opts = dict(rho=2e4, eps=1e-9, max_iter=200000)
+    r = m.sqp(oracle.SqpOptions(tol=1e-8, **opts))
+    assert r["status"] == 0
+    x = r["x"]
+    qp = m.build(x, r["pi"], 0.1, 1)
+    st, info = m.admm(qp, **opts)
+    assert info["s"] <= 1e-9
+    _, pi = m.step(qp, st, x)
+    P = pi.reshape(m.L, 4)
+    nu = st["nu"]
+    nonzero = (np.abs(P) > 1e-6).sum(axis=0)
+    assert nonzero[0] == m.L and np.all(nonzero[1:] >= 1), nonzero
+    o = np.cumsum([0, m.G, m.G, m.B, m.B, m.L, m.L])
+    h = 1e-6
+
+    def grad_free(pm):
+        def lag(y):
+            c4, bal = m.constraints(y)
+            return np.sum(pm * c4) + np.sum(nu * bal)
+        out = []
+        for l in range(m.L):
+            for i in (o[4] + l, o[5] + l):
+                y1 = x.copy(); y1[i] += h
+                y0 = x.copy(); y0[i] -= h
+                out.append((lag(y1) - lag(y0)) / (2 * h))
+        return np.abs(out).max()
+
+    scale = np.abs(P).max() + np.abs(nu).max()
+    assert grad_free(P) <= 1e-8 * scale
+    for k in range(4):
+        Pw = P.copy()
+        Pw[:, k] *= -1
+        assert grad_free(Pw) >= 1e-2 * scale, k
+
+
 def test_sqp_objective_is_invariant_under_relabelling():
     """Renumbering buses and reordering branches describes the same grid, so
     the SQP solution's objective and infeasibility must not change (beyond
