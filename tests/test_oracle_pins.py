@@ -623,6 +623,94 @@ def test_recovered_line_multipliers_satisfy_stationarity():
         assert grad_free(Pw) >= 1e-2 * scale, k
 
 
+def test_kkt_measures_against_their_definitions():
+    """The primal and dual measures of the termination test (Alg. 1) away
+    from any optimum, at a point strictly inside every bound with random
+    multipliers.  Primal: the largest violation of any constraint, equalities
+    in absolute value and inequalities by their negative part.  Dual: the
+    l_inf norm of the gradient of f + pi c + nu bal + angle rows (pi = -u on
+    angmax - dtheta >= 0 and dtheta - angmin >= 0) over every variable but
+    the reference angle, divided by max(1, |grad f|_inf).  Every gradient is
+    a central difference of the objective and constraint values, not the
+    oracle's Jacobians."""
+    g = gg.grid_30bus()
+    m = oracle.Model(g)
+    rng = np.random.default_rng(17)
+    x = _perturbed_point(m, 0.02, rng)
+    v = m.split(x)
+    margin = 1e-3
+    v["pg"][:] = np.clip(v["pg"], g.pmin + margin, g.pmax - margin)
+    v["qg"][:] = np.clip(v["qg"], g.qmin + margin, g.qmax - margin)
+    v["w"][:] = np.clip(v["w"], g.vmin ** 2 + margin, g.vmax ** 2 - margin)
+    ref = int(np.flatnonzero(g.bus_type == 3)[0])
+    P = 10 * rng.standard_normal((m.L, 4))
+    NU = 10 * rng.standard_normal((m.B, 2))
+    UL = rng.standard_normal((m.L, 4))
+    primal, _ = m.kkt(x, P.ravel(), NU.ravel(), UL.ravel())
+
+    def neg(a):
+        return np.maximum(0.0, -np.asarray(a))
+
+    c4, bal = m.constraints(x)
+    dth = v["th"][g.f] - v["th"][g.t]
+    th_nonref = np.delete(v["th"], ref)
+    viol = np.concatenate([
+        np.abs(c4[:, 0]), np.abs(c4[:, 1]), neg(c4[:, 2]), neg(c4[:, 3]),
+        neg(dth - g.angmin), neg(g.angmax - dth), np.abs(bal).ravel(),
+        neg(v["w"] - g.vmin ** 2), neg(g.vmax ** 2 - v["w"]), [abs(v["th"][ref])],
+        neg(th_nonref + 2 * np.pi), neg(2 * np.pi - th_nonref),
+        neg(v["pg"] - g.pmin), neg(g.pmax - v["pg"]), neg(v["qg"] - g.qmin), neg(g.qmax - v["qg"])])
+    assert primal == pytest.approx(viol.max(), rel=1e-12)
+
+    th0 = np.cumsum([0, m.G, m.G, m.B])[3]
+    h = 1e-6
+
+    def fd(fun):
+        out = np.zeros(x.size)
+        for k in range(x.size):
+            y1 = x.copy(); y1[k] += h
+            y0 = x.copy(); y0[k] -= h
+            out[k] = (fun(y1) - fun(y0)) / (2 * h)
+        return out
+
+    gf = fd(m.objective)
+
+    def measure(Pm, NUm, ULm):
+        def lag(y):
+            cy, by = m.constraints(y)
+            vy = m.split(y)
+            d = vy["th"][g.f] - vy["th"][g.t]
+            ang = -ULm[:, 2] * (g.angmax - d) - ULm[:, 3] * (d - g.angmin)
+            return m.objective(y) + np.sum(Pm * cy) + np.sum(NUm * by) + np.sum(ang)
+        grad = fd(lag)
+        grad[th0 + ref] = 0.0
+        return np.abs(grad).max() / max(1.0, np.abs(gf).max())
+
+    # all multipliers at once, then each group alone and large enough that its
+    # terms set the maximum (the measure is an l_inf norm)
+    Z4, Z2 = np.zeros((m.L, 4)), np.zeros((m.B, 2))
+    cases = [(P, NU, UL), (Z4, 1e4 * NU, Z4), (Z4, Z2, 1e4 * UL)]
+    for k in range(4):
+        Pk = Z4.copy()
+        Pk[:, k] = 1e4 * P[:, k]
+        cases.append((Pk, Z2, Z4))
+    # one branch's four multipliers with its end buses' balance multipliers, of
+    # comparable weight: the terms add in the same components, so a wrong sign
+    # of any one term changes the maximum (a lone term's sign would not show)
+    for n in range(24):
+        l = int(rng.integers(m.L))
+        Pk, NUk, ULk = Z4.copy(), Z2.copy(), Z4.copy()
+        Pk[l] = 1e5 * rng.standard_normal(4)
+        NUk[[g.f[l], g.t[l]]] = 3e3 * rng.standard_normal((2, 2))
+        ULk[l, 2:] = 1e5 * rng.standard_normal(2)
+        cases.append((Pk, NUk, ULk))
+    for n, (Pm, NUm, ULm) in enumerate(cases):
+        want = measure(Pm, NUm, ULm)
+        _, got = m.kkt(x, Pm.ravel(), NUm.ravel(), ULm.ravel())
+        assert want > 1e-2, n  # far from stationary: the measure is exercised
+        assert got == pytest.approx(want, rel=1e-6), n
+
+
 def test_sqp_objective_is_invariant_under_relabelling():
     """Renumbering buses and reordering branches describes the same grid, so
     the SQP solution's objective and infeasibility must not change (beyond
