@@ -623,6 +623,51 @@ def test_recovered_line_multipliers_satisfy_stationarity():
         assert grad_free(Pw) >= 1e-2 * scale, k
 
 
+def test_recovered_multipliers_satisfy_qp_stationarity():
+    """pi recovery away from the optimum (Sec. IV-B): at the second SQP
+    iterate of the 30-bus grid the QP's step is far from zero, and its
+    Lagrangian, d'(Hess of pi_old c) d / 2 + pi_new (c + J d) + nu bal, must
+    be stationary in every branch's d_wR and d_wI.  The curvature term is
+    the directional derivative of central differences of pi_old c along d,
+    the linear terms central differences of the constraint values: no
+    Jacobian or Hessian of the oracle enters the check."""
+    g = gg.grid_30bus()
+    m = oracle.Model(g)
+    opts = dict(rho=2e4, eps=1e-10, max_iter=400000)
+    r = m.sqp(oracle.SqpOptions(max_sqp=2, **opts))
+    x, p_old = r["x"], r["pi"]
+    qp = m.build(x, p_old, 0.3, 1)
+    st, info = m.admm(qp, **opts)
+    assert info["s"] <= 1e-10
+    d, p_new = m.step(qp, st, x)
+    assert np.abs(d).max() > 0.1  # far from the optimum: the curvature term matters
+    P, Po, nu = p_new.reshape(m.L, 4), p_old.reshape(m.L, 4), st["nu"]
+    o = np.cumsum([0, m.G, m.G, m.B, m.B, m.L, m.L])
+    h, e = 1e-4, 1e-2
+
+    def lin(y):
+        c4, bal = m.constraints(y)
+        return np.sum(P * c4) + np.sum(nu * bal)
+
+    def curv(y):
+        return np.sum(Po * m.constraints(y)[0])
+
+    def dfun(fun, y, i):
+        y1 = y.copy(); y1[i] += h
+        y0 = y.copy(); y0[i] -= h
+        return (fun(y1) - fun(y0)) / (2 * h)
+
+    res, hd = [], []
+    for l in range(m.L):
+        for i in (o[4] + l, o[5] + l):
+            Hd = (dfun(curv, x + e * d, i) - dfun(curv, x - e * d, i)) / (2 * e)
+            hd.append(Hd)
+            res.append(Hd + dfun(lin, x, i))
+    scale = np.abs(P).max() + np.abs(nu).max()
+    assert np.abs(hd).max() > 1e-2 * scale
+    assert np.abs(res).max() <= 1e-8 * scale
+
+
 def test_kkt_measures_against_their_definitions():
     """The primal and dual measures of the termination test (Alg. 1) away
     from any optimum, at a point strictly inside every bound with random
