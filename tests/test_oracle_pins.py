@@ -207,6 +207,60 @@ def test_line_limit_rows_are_linearised_limits():
             assert row == pytest.approx(-lin, rel=1e-6, abs=1e-8)
 
 
+def test_qp_rows_are_the_shifted_nlp_constraints():
+    """The QP of eq. QPsub at x, on a grid with shunts, taps and phase shifts:
+    the balance rows' right-hand sides are minus the (linear) balances at x;
+    a step d lies in a box exactly when x + d meets the NLP's bounds and
+    |d| <= delta; and it meets an angle row exactly when x + d meets the
+    angle-difference limit.  Membership is tested on random steps, with the
+    NLP side evaluated from its own definition."""
+    base = gg.grid_30bus()
+    g = base.__class__(**{**base.__dict__, "gs": np.linspace(0, 0.03, 30), "bs": np.linspace(0.05, 0, 30),
+                          "tap": np.linspace(0.95, 1.05, 41), "shift": np.linspace(-0.05, 0.05, 41),
+                          "vmin": np.linspace(0.90, 0.96, 30), "vmax": np.linspace(1.10, 1.04, 30)})
+    m = oracle.Model(g)
+    rng = np.random.default_rng(23)
+    x = _perturbed_point(m, 0.05, rng)
+    v = m.split(x)
+    # points near the bounds (each bus has its own band), so that both sides of
+    # every box are exercised
+    v["pg"][::2] = g.pmax[::2] - 0.01
+    v["w"][::3] = g.vmin[::3] ** 2 + 0.02
+    v["w"][1::3] = g.vmax[1::3] ** 2 - 0.02
+    delta = 0.05
+    qp = m.build(x, None, delta, 1)
+    _, bal = m.constraints(x)
+    np.testing.assert_allclose(qp["pdk"], -bal[:, 0], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(qp["qdk"], -bal[:, 1], rtol=0, atol=1e-13)
+
+    def same_membership(lo, hi, val, lb, ub, n=400):
+        for _ in range(n):
+            d = rng.uniform(-2 * delta, 2 * delta)
+            in_box = lo - 1e-12 <= d <= hi + 1e-12
+            in_nlp = lb - 1e-12 <= val + d <= ub + 1e-12 and abs(d) <= delta + 1e-12
+            assert in_box == in_nlp, (lo, hi, val, lb, ub, d)
+
+    for k in range(m.G):
+        same_membership(qp["glp"][k], qp["gup"][k], v["pg"][k], g.pmin[k], g.pmax[k], 100)
+        same_membership(qp["glq"][k], qp["guq"][k], v["qg"][k], g.qmin[k], g.qmax[k], 100)
+    ref = int(np.flatnonzero(g.bus_type == 3)[0])
+    for l in range(m.L):
+        i, j = g.f[l], g.t[l]
+        lo, hi = qp["lo"][l], qp["hi"][l]
+        same_membership(lo[0], hi[0], v["w"][i], g.vmin[i] ** 2, g.vmax[i] ** 2, 40)
+        same_membership(lo[2], hi[2], v["w"][j], g.vmin[j] ** 2, g.vmax[j] ** 2, 40)
+        for e, b in ((1, i), (3, j)):
+            if b == ref:  # the reference angle is held at 0
+                assert lo[e] == hi[e] == -v["th"][b]
+            else:
+                same_membership(lo[e], hi[e], v["th"][b], -2 * np.pi, 2 * np.pi, 20)
+        for _ in range(40):
+            di, dj = rng.uniform(-0.6, 0.6, 2)
+            in_row = qp["alo"][l] - 1e-12 <= di - dj <= qp["ahi"][l] + 1e-12
+            t = (v["th"][i] + di) - (v["th"][j] + dj)
+            assert in_row == (g.angmin[l] - 1e-12 <= t <= g.angmax[l] + 1e-12)
+
+
 # --------------------------------------------------------------------------
 # component updates
 # --------------------------------------------------------------------------
