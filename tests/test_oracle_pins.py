@@ -385,9 +385,60 @@ def test_bus_update_solves_its_kkt_system():
             assert st["zl"][l, 2 * e + 1] == pytest.approx(xs[k], rel=1e-10, abs=1e-12); k += 1
             assert st["zl"][l, 4 + 2 * e] == pytest.approx(xs[-1], rel=1e-10, abs=1e-12)
         assert st["zb"][i, 0] == pytest.approx(xs[-1], rel=1e-10, abs=1e-12)
+        # the angle copies: an unconstrained consensus, the penalty-weighted mean
+        # (0 at the reference bus)
+        rt = sum(st["rl"][l, 5 + 2 * e] for l, e in ends)
+        ct = sum(lam_l[l, 5 + 2 * e] + st["rl"][l, 5 + 2 * e] * st["xl"][l, 5 + 2 * e] for l, e in ends)
+        th_want = 0.0 if g.bus_type[i] == 3 else ct / rt
+        assert st["zb"][i, 1] == pytest.approx(th_want, rel=1e-10, abs=1e-12)
+        for l, e in ends:
+            assert st["zl"][l, 5 + 2 * e] == pytest.approx(th_want, rel=1e-10, abs=1e-12)
         np.testing.assert_allclose(st["nu"][i], sol[n:], rtol=1e-9, atol=1e-9)
         # the balance rows hold exactly
         np.testing.assert_allclose(Am @ xs, [qp["pdk"][i], qp["qdk"][i]], atol=1e-11)
+
+
+def test_admm_residuals_are_their_definitions():
+    """Sec. IV-B residuals of one ADMM iteration from random states with
+    uneven penalties: r = max |x - z| and s = max rho |z+ - z| over every
+    coupling of generators and branches (flows, voltages and angles).  The
+    residuals are l_inf norms, so each coupling group is also made the
+    largest in turn (large multipliers for r, large penalties for s): a group
+    left out of either norm would then show."""
+    g = gg.grid_30bus()
+    m = oracle.Model(g)
+    rng = np.random.default_rng(31)
+    qp = m.build(_perturbed_point(m, 0.05, rng), None, 1.0, 1)
+    groups = {"gen": ("g", slice(None)), "flow": ("l", [0, 1, 2, 3]), "w": ("l", [4, 6]), "th": ("l", [5, 7])}
+
+    def run(boost=None, what=None):
+        st = m.new_state(rho=2e4)
+        for k in ("xl", "zl", "ll", "xg", "zg", "lg"):
+            st[k][...] = rng.standard_normal(st[k].shape)
+        st["rl"][...] = rng.uniform(1e3, 3e4, st["rl"].shape)
+        st["rg"][...] = rng.uniform(1e3, 3e4, st["rg"].shape)
+        if boost is not None:
+            side, cols = groups[boost]
+            key = ("l" if what == "r" else "r") + side
+            st[key][:, cols] *= 1e6 if what == "r" else 1e4
+        z_old = {k: np.array(st[k]) for k in ("zl", "zg")}
+        st, info = m.admm(qp, st, eps=0.0, max_iter=1)
+        rg_ = {"gen": np.abs(st["xg"] - st["zg"]).max()}
+        sg_ = {"gen": (st["rg"] * np.abs(st["zg"] - z_old["zg"])).max()}
+        for name in ("flow", "w", "th"):
+            cols = groups[name][1]
+            rg_[name] = np.abs(st["xl"][:, cols] - st["zl"][:, cols]).max()
+            sg_[name] = (st["rl"][:, cols] * np.abs(st["zl"][:, cols] - z_old["zl"][:, cols])).max()
+        if boost is not None:
+            mine = rg_ if what == "r" else sg_
+            assert mine[boost] == max(mine.values()), (boost, what, mine)
+        assert info["r"] == pytest.approx(max(rg_.values()), rel=1e-12)
+        assert info["s"] == pytest.approx(max(sg_.values()), rel=1e-12)
+
+    run()
+    for name in groups:
+        run(name, "r")
+        run(name, "s")
 
 
 # --------------------------------------------------------------------------
@@ -541,6 +592,64 @@ def test_merit_model_is_second_order_accurate():
     # mu = 0: ared - pred = f-part only (exact quadratic cost) up to the Hessian of
     # the constraints times multipliers, which is second order => error ~ s^3
     assert errs[2] <= errs[0] / 4
+
+
+def test_merit_and_model_against_their_definitions():
+    """The l1 merit phi = f + mu h and the predicted reduction q(0) - q(d)
+    (Sec. II-C) on a grid with tight ratings, so that line limits are
+    violated at x and in the linearisation.  q(d) = grad f d + d' Hess L d / 2
+    + mu m(d), with m(d) the linearised nonlinear constraints plus the linear
+    constraints at x + d (the default merit).  Derivatives along d are
+    symmetric differences of the objective and the constraint values (exact
+    for quadratic f, c11, c13, c14; O(|d|^3) for c12)."""
+    base = gg.grid_30bus()
+    g = base.__class__(**{**base.__dict__, "rate": 0.25 * base.rate})
+    m = oracle.Model(g)
+    rng = np.random.default_rng(29)
+    x = _perturbed_point(m, 0.05, rng)
+    pi = 10 * rng.standard_normal(4 * m.L)
+    qp = m.build(x, pi, 1.0, 1)
+    d = 1e-3 * rng.standard_normal(m.n)
+    mu = 7.0
+    P = pi.reshape(m.L, 4)
+
+    def neg(a):
+        return np.maximum(0.0, -np.asarray(a))
+
+    def nonlinear(c4):
+        return np.abs(c4[:, 0]) + np.abs(c4[:, 1]) + neg(c4[:, 2]) + neg(c4[:, 3])
+
+    def h(y):  # l1 sum of every violation
+        c4, bal = m.constraints(y)
+        v = m.split(y)
+        dth = v["th"][g.f] - v["th"][g.t]
+        ref = np.flatnonzero(g.bus_type == 3)
+        thn = np.delete(v["th"], ref)
+        return (nonlinear(c4).sum() + neg(dth - g.angmin).sum() + neg(g.angmax - dth).sum() + np.abs(bal).sum()
+                + neg(v["w"] - g.vmin ** 2).sum() + neg(g.vmax ** 2 - v["w"]).sum() + np.abs(v["th"][ref]).sum()
+                + neg(thn + 2 * np.pi).sum() + neg(2 * np.pi - thn).sum() + neg(v["pg"] - g.pmin).sum()
+                + neg(g.pmax - v["pg"]).sum() + neg(v["qg"] - g.qmin).sum() + neg(g.qmax - v["qg"]).sum())
+
+    f = m.objective
+
+    def lag(y):
+        return f(y) + np.sum(P * m.constraints(y)[0])
+
+    phx, phxd, pred_mu = m.merit(qp, x, d, mu=mu)
+    _, _, pred0 = m.merit(qp, x, d, mu=0.0)
+    assert phx == pytest.approx(f(x) + mu * h(x), rel=1e-12)
+    assert phxd == pytest.approx(f(x + d) + mu * h(x + d), rel=1e-12)
+    # quadratic model of the Lagrangian along d
+    gd = (f(x + d) - f(x - d)) / 2
+    dHd = lag(x + d) + lag(x - d) - 2 * lag(x)
+    assert pred0 == pytest.approx(-gd - dHd / 2, rel=1e-7, abs=1e-9)
+    # constraint model
+    c0, c1, cm = m.constraints(x)[0], m.constraints(x + d)[0], m.constraints(x - d)[0]
+    lin = c0 + (c1 - cm) / 2
+    assert neg(lin[:, 2:]).sum() > 0  # the linearised limits are violated
+    m_d = nonlinear(lin).sum() + (h(x + d) - nonlinear(c1).sum())
+    # the symmetric difference of c12 errs by O(|d|^3): 3e-11 of mu h here
+    assert abs((pred_mu - pred0) - mu * (h(x) - m_d)) <= 1e-9 * mu * h(x)
 
 
 def _two_bus_dispatch(c2, c1, pd, S=100.0):
