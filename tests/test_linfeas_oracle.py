@@ -56,3 +56,32 @@ def test_projection_fixed_point_and_nonexpansive():
     again, _ = olf.project(m, pa)
     np.testing.assert_allclose(again, pa, atol=1e-10)
     assert np.linalg.norm(pa - pb) <= np.linalg.norm(a - b) * (1 + 1e-9)
+
+
+def test_bounds_are_the_nlp_bounds():
+    """The projection's bounds are those of eq. nlp (opfc1-4 and the
+    reference angle): a random value lies inside exactly when the grid's own
+    limits admit it; wR and wI are free.  Per-bus voltage bands, so that a
+    bound taken from the wrong bus or left unsquared shows."""
+    base = gg.grid_30bus()
+    g = base.__class__(**{**base.__dict__, "vmin": np.linspace(0.90, 0.96, 30), "vmax": np.linspace(1.10, 1.04, 30)})
+    m = oracle.Model(g)
+    _, _, lo, hi = olf.linear_constraints(m)
+    G, B, L = m.G, m.B, m.L
+    rng = np.random.default_rng(41)
+    ref = int(np.flatnonzero(g.bus_type == 3)[0])
+    blocks = [(0, G, g.pmin, g.pmax, 4.0), (G, G, g.qmin, g.qmax, 2.0),
+              (2 * G, B, g.vmin ** 2, g.vmax ** 2, 1.5), (2 * G + B, B, None, None, 8.0)]
+    for o, n, bl, bu, span in blocks:
+        for k in range(n):
+            for val in rng.uniform(-span, span, 50):
+                inside = lo[o + k] <= val <= hi[o + k]
+                if bl is None:  # angles: [-2 pi, 2 pi], the reference held at 0
+                    want = val == 0.0 if k == ref else -2 * np.pi <= val <= 2 * np.pi
+                else:
+                    want = bl[k] <= val <= bu[k]
+                assert inside == want, (o, k, val)
+        if bl is None:
+            assert lo[o + ref] == hi[o + ref] == 0.0
+    assert np.all(np.isinf(lo[2 * G + 2 * B:])) and np.all(np.isinf(hi[2 * G + 2 * B:]))
+    assert lo.size == 2 * G + 2 * B + 2 * L
