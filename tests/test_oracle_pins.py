@@ -337,6 +337,58 @@ def test_line_qp_brute_force_never_beats_it():
         assert f_or <= fy.min() + 1e-12
 
 
+def test_line_update_solves_the_line_subproblem():
+    """eq. line_kernel from an ADMM state with a different penalty on every
+    coupling: the branch result of one iteration must minimise
+    1/2 d'QH d + gH'd + sum over flows and voltage copies of
+    lambda (v - z) + rho/2 (v - z)^2 (flows v = F d + f0) over the box, the
+    line-limit rows and the angle rows, written out here and solved by SLSQP
+    from scratch (the oracle's solution, being exact, can only be better)."""
+    from scipy.optimize import minimize
+
+    g = gg.grid_30bus()
+    m = oracle.Model(g)
+    rng = np.random.default_rng(37)
+    x = _perturbed_point(m, 0.05, rng)
+    qp = m.build(x, 10 * rng.standard_normal(4 * m.L), 0.3, 1)
+    st = m.new_state(rho=2e4)
+    st["zl"][...] = 0.05 * rng.standard_normal(st["zl"].shape)
+    st["ll"][...] = 300 * rng.standard_normal(st["ll"].shape)
+    st["rl"][...] = rng.uniform(1e3, 3e4, st["rl"].shape)
+    z0, l0, r0 = np.array(st["zl"]), np.array(st["ll"]), np.array(st["rl"])
+    st, _ = m.admm(qp, st, eps=0.0, max_iter=1)
+    for l in range(m.L):
+        QH, gH = qp["QH"][l].reshape(4, 4), qp["gH"][l]
+        F, f0 = qp["F"][l].reshape(4, 4), qp["f0"][l]
+
+        def obj(db):
+            df = F @ db + f0
+            return (0.5 * db @ QH @ db + gH @ db + l0[l, :4] @ (df - z0[l, :4])
+                    + 0.5 * r0[l, :4] @ (df - z0[l, :4]) ** 2 + l0[l, 4:] @ (db - z0[l, 4:])
+                    + 0.5 * r0[l, 4:] @ (db - z0[l, 4:]) ** 2)
+
+        Gm, gr = qp["G"][l].reshape(2, 4), qp["grhs"][l]
+        cons = [{"type": "ineq", "fun": lambda db, e=e: gr[e] - Gm[e] @ db} for e in range(2) if gr[e] < 1e29]
+        cons += [{"type": "ineq", "fun": lambda db: db[1] - db[3] - qp["alo"][l]},
+                 {"type": "ineq", "fun": lambda db: qp["ahi"][l] - (db[1] - db[3])}]
+        lo, hi = qp["lo"][l], qp["hi"][l]
+
+        def feasible(v):
+            return np.all(v >= lo - 1e-12) and np.all(v <= hi + 1e-12) and all(c["fun"](v) >= -1e-9 for c in cons)
+
+        # the best feasible point two independent solvers find from the same start
+        start = np.clip(z0[l, 4:], lo, hi)
+        found = [minimize(obj, start, method="SLSQP", bounds=list(zip(lo, hi)), constraints=cons,
+                          options=dict(ftol=1e-15, maxiter=1000)).x,
+                 minimize(obj, start, method="trust-constr", bounds=list(zip(lo, hi)), constraints=cons,
+                          options=dict(gtol=1e-12, xtol=1e-14, maxiter=3000)).x]
+        best = min(obj(v) for v in found if feasible(v))
+        mine = st["xl"][l, 4:]
+        assert feasible(mine), l
+        assert obj(mine) <= best + 1e-9 * (1 + abs(best)), l
+        np.testing.assert_allclose(st["xl"][l, :4], F @ mine + f0, rtol=0, atol=1e-12)
+
+
 def test_bus_update_solves_its_kkt_system():
     """eq. bus_kernel: the closed form equals a dense solve of the bus QP's KKT system."""
     g = gg.grid_30bus()
