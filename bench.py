@@ -286,6 +286,11 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": m["launches"],
         "clocks": m["clocks"],
         "launch_shape": m["launch_shape"],
+        # the paper's timings for grids of similar size (Table II): other grids, hardware and tolerance,
+        # so context only, not a ratio
+        "paper_context": {"cases": "case2383wp, case2736sp, case2737sop, case2746wop (2,383-2,746 buses)",
+                          "seconds_per_solve": [11.79, 11.07, 10.62, 10.58], "sqp_iters": 2, "tolerance": 1e-3,
+                          "hardware": "Quadro GV100 (Volta), ExaAdmm.jl", "source": "Table II"},
     }
     if "e2e_s" in m:
         out["e2e"] = {"value": m["e2e_conv"] / m["e2e_s"] if m["e2e_s"] > 0 else 0.0, "unit": "solves/s",
