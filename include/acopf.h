@@ -350,9 +350,17 @@ acopf_status acopf_autotune(acopf_handle h, const char* cache_path, int32_t iter
  * calls whose work overlaps on the GPU (two handles on different streams, or
  * two threads) race on it and must be serialised by the caller.
  *
+ * An instance whose ADMM residual test passed in the handle's last
+ * admm_solve_qp is skipped, as admm_iterate skips it.  The sweep is not timed
+ * by acopf_profile.
+ *
  * n >= 1 iterations, o as for admm_iterate.  rs and iters are caller-owned
  * DEVICE buffers: rs receives 2*K doubles (r of every instance, then s) of
- * the last iteration, iters K int32 iteration counts, K = number of instances.
+ * the last iteration, iters K int32 iteration counts, K = number of instances;
+ * the same values are copied (device to device) into the handle's own record,
+ * so acopf_get_residuals reports them afterwards.  The device address of the
+ * fixed array is looked up once per device and assumes that the device's
+ * primary context lives until the process exits (no cudaDeviceReset).
  * Errors: EINVAL for a NULL buffer, bad options, or a handle with more than
  * ACOPF_STATIC_MAX_INSTANCES instances; ENOTREADY before any QP was built;
  * ETIMEOUT as admm_iterate; ECUDA if the device address cannot be obtained. */

@@ -23,6 +23,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -966,13 +967,20 @@ constexpr size_t kStaticBytes = kStaticHeader + kStaticSlots + kStaticDone + kSt
 static __device__ __align__(256) unsigned char g_sweep_scratch[kStaticBytes];
 
 // Device address of g_sweep_scratch per device ordinal (host-side copies of the
-// symbol are only stand-ins, not device addresses).
-static void* g_scratch_addr[64] = {};
+// symbol are only stand-ins, not device addresses).  Looked up once per device
+// and published atomically, so concurrent first calls on one device are safe
+// (both store the same address).  The address belongs to the device's primary
+// context: it assumes that context lives for the whole process (a
+// cudaDeviceReset would invalidate it).
+static std::atomic<void*> g_scratch_addr[64];
 
-__global__ void k_static_init(Dev d) {
+// The finished flags start from the handle's own (handle_done): an instance
+// whose ADMM residual test passed in the last admm_solve_qp is skipped here
+// exactly as admm_iterate skips it.
+__global__ void k_static_init(Dev d, const int* handle_done) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < d.K) {
-    d.admm_done[k] = d.ctl[k].result == ACOPF_RUNNING ? 0 : 1;
+    d.admm_done[k] = handle_done[k];
     d.rho_fac[k] = 1.0;
   }
 }
@@ -980,6 +988,7 @@ __global__ void k_static_init(Dev d) {
 template <typename T>
 acopf_status run_sweep_static(Ctx& c, const admm_options& o, int n, double* rs, int* iters, unsigned char* base) {
   Dev d = c.d;
+  const int* handle_done = c.d.admm_done;
   d.bar = (unsigned*)base;
   d.err = (int*)(base + 2 * sizeof(unsigned));
   d.res_slots = (unsigned long long*)(base + kStaticHeader);
@@ -1002,7 +1011,7 @@ acopf_status run_sweep_static(Ctx& c, const admm_options& o, int n, double* rs, 
   p.rb_mu = o.rb_mu;
   p.rb_tau = o.rb_tau;
   p.stages = c.sweep_stages;
-  p.profile = c.profiling ? 1 : 0;
+  p.profile = 0;  // not timed: acopf_profile covers the handle's own sweeps only
   int threads = c.block_threads;
   size_t smem = sweep_smem<T>(d.K, threads, c.sweep_stages);
   cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1018,7 +1027,7 @@ acopf_status run_sweep_static(Ctx& c, const admm_options& o, int n, double* rs, 
   if (blocks < 1) blocks = 1;
   // what must start at zero: barrier counters, error flag, residual slots
   cudaMemsetAsync(base, 0, kStaticHeader + sizeof(unsigned long long) * 4 * d.K, c.stream);
-  k_static_init<<<nblk(d.K, 256), 256, 0, c.stream>>>(d);
+  k_static_init<<<nblk(d.K, 256), 256, 0, c.stream>>>(d, handle_done);
   void* args[] = {&p};
   cudaError_t e = cudaLaunchCooperativeKernel((void*)k_sweep<T>, dim3(blocks), dim3(threads), args, smem, c.stream);
   c.launches += 2;
@@ -1026,6 +1035,10 @@ acopf_status run_sweep_static(Ctx& c, const admm_options& o, int n, double* rs, 
     c.last_error = std::string("admm_iterate_static launch: ") + cudaGetErrorString(e);
     return ACOPF_ECUDA;
   }
+  // the handle's own residual record follows this sweep too (acopf_get_residuals
+  // reads it); device-to-device copies into memory the handle already owns
+  cudaMemcpyAsync(c.d.admm_rs, rs, sizeof(double) * 2 * d.K, cudaMemcpyDeviceToDevice, c.stream);
+  cudaMemcpyAsync(c.d.admm_iters, iters, sizeof(int) * d.K, cudaMemcpyDeviceToDevice, c.stream);
   if (o.rb_period > 0) {
     long m = d.L > d.G ? d.L : d.G;
     k_commit_rho<<<nblk(m, 256), 256, 0, c.stream>>>(d);
@@ -1072,16 +1085,16 @@ extern "C" acopf_status admm_iterate_static(acopf_handle h, int32_t n, const adm
     return ACOPF_ECUDA;
   }
   // one-time set-up per device, with that device current
-  if (!g_scratch_addr[c->device]) {
-    void* ptr = nullptr;
+  void* ptr = g_scratch_addr[c->device].load(std::memory_order_acquire);
+  if (!ptr) {
     e = cudaGetSymbolAddress(&ptr, g_sweep_scratch);
     if (e != cudaSuccess || !ptr) {
       c->last_error = std::string("admm_iterate_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
       return ACOPF_ECUDA;
     }
-    g_scratch_addr[c->device] = ptr;
+    g_scratch_addr[c->device].store(ptr, std::memory_order_release);
   }
-  unsigned char* base = (unsigned char*)g_scratch_addr[c->device];
+  unsigned char* base = (unsigned char*)ptr;
   acopf_status s = c->precision == ACOPF_MIXED ? run_sweep_static<float>(*c, o, n, rs, iters, base)
                                                : run_sweep_static<double>(*c, o, n, rs, iters, base);
   if (s) return s;
