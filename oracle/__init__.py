@@ -106,6 +106,10 @@ def lib():
         L.og_merit.argtypes = [C.c_void_p, C.POINTER(_QP), DP, DP, C.c_double, C.c_int, DP, DP, DP]
         L.og_kkt.argtypes = [C.c_void_p, DP, DP, DP, DP, C.c_int, DP, DP]
         L.og_sqp.argtypes = [C.c_void_p, C.POINTER(_SqpOpts), DP, DP, DP, C.POINTER(_SqpInfo), DP, C.c_int]
+        L.og_tr_update.argtypes = [C.POINTER(_SqpOpts), C.c_double, C.c_double, C.c_double, C.c_double,
+                                   C.POINTER(C.c_int)]
+        L.og_tr_update.restype = C.c_double
+        L.og_violations.argtypes = [C.c_void_p, DP, C.c_int, DP, DP]
         _lib = L
     return _lib
 
@@ -139,6 +143,19 @@ class SqpOptions:
     rb_period: int = 0
     rb_mu: float = 10.0
     rb_tau: float = 2.0
+
+
+def _sqp_opts(o: SqpOptions):
+    return _SqpOpts(o.mu, o.tol, o.step_tol, o.delta0, o.delta_max, o.delta_min, o.rho, o.max_sqp,
+                    o.warm_lambda, _AdmmOpts(o.eps, o.max_iter, o.use_angle, o.rb_period, o.rb_mu, o.rb_tau))
+
+
+def tr_update(opts: SqpOptions, delta, dnorm, ared, pred):
+    """Ratio test and trust-region update of Alg. 1: (accepted, new radius)."""
+    acc = C.c_int()
+    nd = lib().og_tr_update(C.byref(_sqp_opts(opts)), float(delta), float(dnorm), float(ared), float(pred),
+                            C.byref(acc))
+    return bool(acc.value), nd
 
 
 class Model:
@@ -213,6 +230,12 @@ class Model:
     def objective(self, x):
         return lib().og_objective(self._h, _dp(_f64(x)))
 
+    def violations(self, x, use_angle=1):
+        """(l1 sum, l_inf maximum) of every constraint violation at x."""
+        a, b = C.c_double(), C.c_double()
+        lib().og_violations(self._h, _dp(_f64(x)), int(use_angle), C.byref(a), C.byref(b))
+        return a.value, b.value
+
     # --------------------------------------------------------------- QP data
     def new_qp(self):
         arrs = {n: np.zeros(w * max(self._count(c), 1)) for n, w, c in _QP_FIELDS}
@@ -232,6 +255,11 @@ class Model:
         st = AdmmState(self, arrs)
         lib().og_admm_cold(self._h, C.byref(st.s), float(rho), 0)
         return st
+
+    def cold(self, state, rho=2e4, keep_lambda=0):
+        """ADMM restart for a new QP: d, z = 0; multipliers reset unless kept."""
+        lib().og_admm_cold(self._h, C.byref(state.s), float(rho), int(keep_lambda))
+        return state
 
     def admm(self, qp, state=None, rho=2e4, eps=1e-4, max_iter=20000, use_angle=1, rb_period=0, rb_mu=10.0,
              rb_tau=2.0):
@@ -265,8 +293,7 @@ class Model:
 
     def sqp(self, opts: SqpOptions | None = None, x0=None, hist_cap=200):
         o = opts or SqpOptions()
-        so = _SqpOpts(o.mu, o.tol, o.step_tol, o.delta0, o.delta_max, o.delta_min, o.rho, o.max_sqp,
-                      o.warm_lambda, _AdmmOpts(o.eps, o.max_iter, o.use_angle, o.rb_period, o.rb_mu, o.rb_tau))
+        so = _sqp_opts(o)
         x0 = self.flat_start() if x0 is None else _f64(x0)
         x = np.zeros(self.n)
         pi = np.zeros(4 * self.L + 1)

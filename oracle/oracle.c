@@ -985,6 +985,27 @@ void og_kkt(const og_model* m, const double* x, const double* pi, const double* 
 }
 
 /* ------------------------------------------------------------------ SQP */
+/* Step acceptance and trust-region update of Alg. 1.
+ * Acceptance is the ratio test of Sec. II-C as printed: the actual merit
+ * reduction ared = phi_1(x) - phi_1(x + d) must be positive and so must
+ * ared / pred, pred = q(0) - q(d); with ared > 0 that is pred > 0 (a zero or
+ * non-finite pred rejects).  Alg. 1 prints only Delta+ >= Delta on acceptance
+ * and Delta+ <= Delta on rejection; the rules it carries as comments give the
+ * constants: an accepted step on the trust-region boundary (|d|_inf >= 0.99
+ * Delta, the boundary up to rounding) doubles Delta, capped at delta_max (the
+ * commented max{2 Delta, Delta-bar} read as a cap); an accepted interior step
+ * keeps Delta; a rejected step sets Delta = 0.5 min(Delta, |d|_inf). */
+double og_tr_update(const og_sqp_opts* o, double delta, double dnorm, double ared, double pred, int* accept) {
+  int acc = isfinite(ared) && isfinite(pred) && ared > 0 && pred > 0;
+  *accept = acc;
+  if (acc) return dnorm >= 0.99 * delta ? dmin(2 * delta, o->delta_max) : delta;
+  return 0.5 * dmin(delta, dnorm);
+}
+
+void og_violations(const og_model* m, const double* x, int use_angle, double* h1, double* hinf) {
+  violations(m, x, use_angle, h1, hinf);
+}
+
 static int all_finite(const double* v, int n) {
   for (int k = 0; k < n; ++k)
     if (!isfinite(v[k])) return 0;
@@ -1043,15 +1064,13 @@ int og_sqp(const og_model* m, const og_sqp_opts* o, const double* x0, double* x,
     double phx, phxd, pred;
     og_merit(m, &qp, x, d, o->mu, o->admm.use_angle, &phx, &phxd, &pred);
     double ared = phx - phxd;
-    int accept = isfinite(ared) && isfinite(pred) && ared > 0 && pred > 0;
+    int accept = 0;
+    delta = og_tr_update(o, delta, dn, ared, pred, &accept);
     if (accept) {
       for (int t2 = 0; t2 < n; ++t2) x[t2] += d[t2];
       memcpy(pi, pin, sizeof(double) * 4 * L);
       acc++;
-      if (dn >= 0.99 * delta) delta = dmin(2 * delta, o->delta_max);
       og_kkt(m, x, pi, st.nu, st.ul, o->admm.use_angle, &primal, &dual);
-    } else {
-      delta = 0.5 * dmin(delta, dn);
     }
     if (hist && k < hist_cap) {
       double* hr = hist + OG_HIST_W * k;

@@ -147,6 +147,11 @@ void og_kkt(const og_model* m, const double* x, const double* pi, const double* 
 int og_sqp(const og_model* m, const og_sqp_opts* o, const double* x0, double* x, double* pi,
            og_sqp_info* info, double* hist, int hist_cap);
 
+/* ratio test and trust-region update of Alg. 1: returns the new radius, *accept 0/1 */
+double og_tr_update(const og_sqp_opts* o, double delta, double dnorm, double ared, double pred, int* accept);
+/* l1 sum and l_inf maximum of every constraint violation at x (h of the merit function) */
+void og_violations(const og_model* m, const double* x, int use_angle, double* h1, double* hinf);
+
 #ifdef __cplusplus
 }
 #endif
