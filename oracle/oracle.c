@@ -429,6 +429,16 @@ static double kkt_try(const lqp* P, const int* W, int nw, int nmust, double x[4]
   double viol = 0, dviol = 0;
   int inW[NROW] = {0};
   for (int k = 0; k < nw; ++k) inW[W[k]] = 1;
+  /* a KKT point satisfies its working set's rows as equalities; a (nearly)
+   * singular system can return a point that does not, which is no solution */
+  for (int k = 0; k < 4 + nw; ++k)
+    if (!isfinite(rhs[k])) return -1.0;
+  for (int k = 0; k < nw; ++k) {
+    const double* a = P->A[W[k]];
+    double an = fabs(a[0]) + fabs(a[1]) + fabs(a[2]) + fabs(a[3]);
+    double ax = a[0] * x[0] + a[1] * x[1] + a[2] * x[2] + a[3] * x[3];
+    if (fabs(ax - P->b[W[k]]) > 1e-9 * (1.0 + fabs(P->b[W[k]]) + an * xs)) return -1.0;
+  }
   for (int k = 0; k < NROW; ++k) {
     if (inW[k] || P->b[k] >= 0.5 * BIG) continue;
     double ax = P->A[k][0] * x[0] + P->A[k][1] * x[1] + P->A[k][2] * x[2] + P->A[k][3] * x[3];
