@@ -94,13 +94,20 @@ typedef struct {
   int32_t warm;          /* 0: every QP starts from d = 0, lambda = 0;  1: lambda (and the
                             line multipliers) carry over from the previous QP */
   double alm_beta;       /* augmented-Lagrangian penalty, as a multiple of max_i Q_ii */
-  double alm_tol;        /* line-limit feasibility/complementarity tolerance */
+  double alm_tol;        /* line-limit feasibility/complementarity tolerance (default 1e-14; the
+                            FP32 sweep uses at least 2e-6) */
   int32_t alm_max_outer; /* multiplier updates per line subproblem */
   int32_t newton_max;    /* projected Newton steps per multiplier update */
   int64_t spin_limit;    /* clock cycles a CTA waits at a device-wide barrier before giving up */
   int32_t rb_period;     /* residual balancing every rb_period iterations (0: fixed rho):   */
   double rb_mu, rb_tau;  /* rho *= rb_tau if r > rb_mu s, rho /= rb_tau if s > rb_mu r; the
                             adapted penalties carry over to the next QP when warm = 1     */
+  int32_t line_solver;   /* how the FP64 sweep solves each line subproblem (eq. line_kernel):
+                            0 (default): exactly, by the dual active-set method of Goldfarb and
+                            Idnani, a subproblem with no feasible point falling back to 1;
+                            1: the augmented Lagrangian of Sec. IV-B (alm_* and newton_max above).
+                            The FP32 sweep always uses the augmented Lagrangian, whose final
+                            solves are refined in twice the working precision */
 } admm_options;
 
 typedef struct {
@@ -184,7 +191,12 @@ acopf_status acopf_set_stream(acopf_handle h, void* cuda_stream);
 acopf_status acopf_set_allocator(acopf_handle h, void* (*alloc)(size_t bytes, void* ctx),
                                  void (*release)(void* ptr, void* ctx), void* ctx);
 
-/* Replace the loads of instance inst (host arrays of its nbus). */
+/* Replace the loads p_i^d, q_i^d of instance inst (Sec. III-A, eq. acopf: the
+ * right-hand sides of the bus power balances opfc5-opfc6), in p.u.: host
+ * arrays of the instance's nbus.  The copies are queued on the handle's
+ * stream: pageable arrays are read during the call, page-locked ones must
+ * stay unchanged until the stream has reached the copy.  Takes effect at the
+ * next QP build.  Errors: EINVAL for a bad handle, instance or NULL array. */
 acopf_status acopf_set_loads(acopf_handle h, int32_t inst, const double* pd, const double* qd);
 
 /* Run Algorithm 1 from a flat start (or from the warm start set below) on
@@ -233,7 +245,24 @@ acopf_status acopf_project_linear(acopf_handle h, double rho, double eps, int32_
 acopf_status acopf_set_warm_start(acopf_handle h, int32_t inst, const double* x0, const double* lambda0,
                                   const double* rho);
 
+/* The iterate of instance inst after the last solve, in the variables of
+ * Sec. III-A (eq. acopf): generator dispatch p_g, q_g; bus voltage magnitude
+ * sqrt(w_i) and angle theta_i; branch products w^R_ij, w^I_ij; and the
+ * objective of eq. acopf at that point (costs per MW, c2 (S p)^2 + c1 S p +
+ * c0 with S = base_mva).  out's arrays are caller-owned host arrays (NULL to
+ * skip one).  Synchronises the handle's stream.  Errors: EINVAL for a bad
+ * handle, instance or out. */
 acopf_status acopf_get_solution(acopf_handle h, int32_t inst, acopf_solution* out);
+/* Termination measures of instance inst (Alg. 1: the SQP stops when the
+ * primal and dual infeasibility of eq. acopf are both within tol, or the
+ * accepted step is below step_tol; the columns reported in Tables I-II):
+ * primal = l_inf of every constraint violation in p.u.; dual = l_inf of the
+ * gradient of the Lagrangian (bus balance multipliers, pi and angle-row
+ * multipliers of the last QP, projected at active bounds) over max(1,
+ * ||grad f||_inf); r_inf, s_inf = the last ADMM residuals of Sec. IV-B;
+ * delta = the trust radius; iteration counts and the acopf_result.
+ * Synchronises the handle's stream.  Errors: EINVAL for a bad handle,
+ * instance or out. */
 acopf_status acopf_get_residuals(acopf_handle h, int32_t inst, acopf_residuals* out);
 
 /* Per-SQP-iteration history of the last sqp_solve for instance inst, 12 values
@@ -309,9 +338,13 @@ acopf_status acopf_get_profile_phases(acopf_handle h, double* ns);
 
 /* Launch shape of the ADMM sweep (the autotuner's knobs): threads per CTA
  * (32..256, multiple of 32; 0 keeps), resident CTAs per SM (0 = as many as
- * fit; -1 keeps), and for the FP32 sweep how branch records reach the line
- * solves: 1 or 2 shared-memory tile buffers filled by bulk async copies, or 0
- * = read in place from global memory (-1 keeps). */
+ * fit; -1 keeps), and how branch records reach the line solves (-1 keeps):
+ * 0 = read in place from global memory every iteration; 1 or 2 (FP32 sweep)
+ * = shared-memory tile buffers filled by bulk async copies; 3 = loaded once
+ * per sweep into registers, together with every other piece of static data
+ * (instance ids, bus-task slots, bus loads), which needs a co-resident grid
+ * with one thread per generator or branch and at most two bus tasks per
+ * warp, and residual balancing off -- otherwise the sweep runs as with 0. */
 acopf_status acopf_tune(acopf_handle h, int32_t block_threads, int32_t ctas_per_sm, int32_t sweep_stages);
 
 /* Autotuner of the sweep's launch shape.  If cache_path (may be NULL) names a
@@ -319,8 +352,8 @@ acopf_status acopf_tune(acopf_handle h, int32_t block_threads, int32_t ctas_per_
  * precision and the binary orders of magnitude of the instance, bus and
  * branch counts -- that shape is applied.  Otherwise the QP at the current
  * iterate is built (delta 1, rho 2e4) and every shape of {64, 128, 256}
- * threads x {as many CTAs per SM as fit, 1} x {0, 1, 2} branch-tile buffers
- * (FP32 sweep; FP64: 0) is timed over iters fixed ADMM iterations with CUDA
+ * threads x {as many CTAs per SM as fit, 1} x record access {0, 1, 2, 3}
+ * (FP32 sweep; FP64: {0, 3}, see acopf_tune) is timed over iters fixed ADMM iterations with CUDA
  * events; the fastest is applied and written to the cache (other keys are
  * kept).  shape_out (3 ints: threads, CTAs per SM, buffers) and us_per_iter
  * (-1 when taken from the cache) may be NULL.  Resets the ADMM state: call it

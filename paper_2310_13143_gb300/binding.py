@@ -47,7 +47,7 @@ class admm_options(C.Structure):
                 ("warm", C.c_int32),
                 ("alm_beta", C.c_double), ("alm_tol", C.c_double), ("alm_max_outer", C.c_int32),
                 ("newton_max", C.c_int32), ("spin_limit", C.c_int64), ("rb_period", C.c_int32),
-                ("rb_mu", C.c_double), ("rb_tau", C.c_double)]
+                ("rb_mu", C.c_double), ("rb_tau", C.c_double), ("line_solver", C.c_int32)]
 
 
 class sqp_options(C.Structure):

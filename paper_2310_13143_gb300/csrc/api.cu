@@ -146,13 +146,14 @@ void admm_default_options(admm_options* o) {
   o->max_iter = 20000;
   o->warm = 1;
   o->alm_beta = 10.0;
-  o->alm_tol = 1e-11;
+  o->alm_tol = 1e-14;
   o->alm_max_outer = 50;
   o->newton_max = 20;
   o->spin_limit = 4000000000LL;
   o->rb_period = 0;
   o->rb_mu = 10.0;
   o->rb_tau = 2.0;
+  o->line_solver = 0;
 }
 
 void sqp_default_options(sqp_options* o) {
@@ -612,7 +613,7 @@ acopf_status acopf_tune(acopf_handle h, int32_t block_threads, int32_t ctas_per_
   }
   if (ctas_per_sm >= 0) c->ctas_per_sm = ctas_per_sm;
   if (sweep_stages >= 0) {
-    if (sweep_stages > 2) return fail(c, ACOPF_EINVAL, "acopf_tune: sweep_stages must be 0, 1 or 2");
+    if (sweep_stages > 3) return fail(c, ACOPF_EINVAL, "acopf_tune: sweep_stages must be 0, 1, 2 or 3");
     c->sweep_stages = sweep_stages;
   }
   drop_graph(c);  // the launch shape is baked into a captured graph
@@ -728,7 +729,7 @@ static acopf_status reset_control(Ctx* c, const sqp_options& o, bool fresh) {
 static acopf_status check_admm(const admm_options& a, Ctx* c) {
   if (!(a.rho > 0) || !(a.eps >= 0) || !(a.eps_dual >= 0) || a.max_iter < 1 || a.alm_max_outer < 1 || a.newton_max < 1 ||
       !(a.alm_beta > 0) || a.spin_limit < 1 || a.rb_period < 0 ||
-      (a.rb_period > 0 && (!(a.rb_mu > 1) || !(a.rb_tau > 1))))
+      (a.rb_period > 0 && (!(a.rb_mu > 1) || !(a.rb_tau > 1))) || a.line_solver < 0 || a.line_solver > 1)
     return fail(c, ACOPF_EINVAL, "admm options out of range");
   return ACOPF_OK;
 }
@@ -876,7 +877,7 @@ static std::string tune_key(Ctx* c) {
     return k;
   };
   char buf[128];
-  snprintf(buf, sizeof(buf), "sm%d-%s-K%d-B%d-L%d", c->num_sms, c->precision == ACOPF_MIXED ? "mixed" : "fp64",
+  snprintf(buf, sizeof(buf), "v2-sm%d-%s-K%d-B%d-L%d", c->num_sms, c->precision == ACOPF_MIXED ? "mixed" : "fp64",
            lg(c->d.K), lg(c->d.B), lg(c->d.L));
   return buf;
 }
@@ -906,7 +907,7 @@ static bool cache_lookup(const char* path, const std::string& key, int shape[3])
     if (sscanf(p, "\"block_threads\": %d", &bt) != 1 || sscanf(q, "\"ctas_per_sm\": %d", &cps) != 1 ||
         sscanf(r, "\"stages\": %d", &st) != 1)
       continue;
-    if (bt < 32 || bt > 256 || bt % 32 || cps < 0 || st < 0 || st > 2) continue;
+    if (bt < 32 || bt > 256 || bt % 32 || cps < 0 || st < 0 || st > 3) continue;
     shape[0] = bt; shape[1] = cps; shape[2] = st;
     return true;
   }
@@ -959,10 +960,14 @@ acopf_status acopf_autotune(acopf_handle h, const char* cache_path, int32_t iter
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     const int threads[3] = {64, 128, 256};
-    const int nst = c->precision == ACOPF_MIXED ? 2 : 0;
+    // record access: in place (0), staged tiles (1, 2; FP32 sweep only), held in registers (3)
+    const int modes_mixed[4] = {0, 1, 2, 3}, modes_fp64[2] = {0, 3};
+    const int* modes = c->precision == ACOPF_MIXED ? modes_mixed : modes_fp64;
+    const int nmodes = c->precision == ACOPF_MIXED ? 4 : 2;
     for (int ti = 0; ti < 3; ++ti)
       for (int cps = 0; cps <= 1; ++cps)
-        for (int st = 0; st <= nst; ++st) {
+        for (int mi = 0; mi < nmodes; ++mi) {
+          const int st = modes[mi];
           c->block_threads = threads[ti];
           c->ctas_per_sm = cps;
           c->sweep_stages = st;

@@ -17,7 +17,7 @@ struct Tol;
 template <>
 struct Tol<double> {
   static constexpr double newton = 1e-13;
-  static constexpr double alm = 1e-11;
+  static constexpr double alm = 1e-14;
 };
 template <>
 struct Tol<float> {
@@ -152,6 +152,24 @@ ACOPF_HD inline T resid_dot2(T r, const T a[4], const T x[4]) {
   return s + e;
 }
 
+// A sum of products accumulated in twice the working precision (the same
+// Dot2 scheme), rounded once by value().
+template <typename T>
+struct Dot2Acc {
+  T s, e;
+  ACOPF_HD inline explicit Dot2Acc(T r) : s(r), e(T(0)) {}
+  ACOPF_HD inline void add(T a, T b) {  // s + e += a b
+    T pr = a * b;
+    T pe = fma(a, b, -pr);
+    T t = s + pr;
+    T z = t - s;
+    T se = (s - (t - z)) + (pr - z);
+    s = t;
+    e += se + pe;
+  }
+  ACOPF_HD inline T value() const { return s + e; }
+};
+
 // Box-constrained strictly convex QP  min 1/2 x'Hx + b'x,  lo <= x <= hi,
 // by the primal active-set method from the feasible start x.  Bit i of fx:
 // variable i held at a bound (at lo when bit i of hiside is clear).  Returns
@@ -264,6 +282,317 @@ ACOPF_HD inline int box_qp(const T h[10], const T b[4], const T lo[4], const T h
     hs &= ~(1u << worst);
   }
   return it;
+}
+
+// ------------------------------------------------ exact line QP (dual method)
+// The same subproblem solved exactly by the dual active-set method of
+// Goldfarb and Idnani ("A numerically stable dual method for solving strictly
+// convex quadratic programs", Math. Programming 27, 1983): start from the
+// unconstrained minimiser -Q^-1 c, repeatedly add the most violated
+// constraint, taking full (primal) steps or partial (dual) steps that drop a
+// constraint whose multiplier would turn negative, with Q^-1 and the active
+// normals held as J = L^-T (rotated) and the triangular factor R, J'N = [R;0].
+// Every step raises the dual objective, so it ends in a few steps at the
+// unique KKT point; no feasible start is needed.  Constraint p in the form
+// n_p'x >= b_p:
+//   0..3  x_v >= lo_v          4..7  -x_v >= -hi_v
+//   8, 9  -R_r x >= -rb_r      (line limits, when on)
+//   10    -(x1 - x3) >= -ahi   11  x1 - x3 >= alo   (angle rows, when set)
+template <typename T>
+ACOPF_HD inline bool gi_row(const LineQP<T>& P, int p, T n[4], T& b) {
+  bool on = true;
+  b = T(0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) n[i] = T(0);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    if (p == v) { n[v] = T(1); b = P.lo[v]; }
+    if (p == 4 + v) { n[v] = T(-1); b = -P.hi[v]; }
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+    if (p == 8 + r) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) n[i] = -P.R[r][i];
+      b = -P.rb[r];
+      on = P.on[r];
+    }
+  if (p == 10) { n[1] = T(-1); n[3] = T(1); b = -P.ahi; on = P.ang; }
+  if (p == 11) { n[1] = T(1); n[3] = T(-1); b = P.alo; on = P.ang; }
+  return on;
+}
+
+// Givens rotation of columns a, b of J (applied as J <- J G')
+template <typename T>
+ACOPF_HD inline void gi_rot_cols(T J[4][4], int a, int b, T c, T s) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    T ja = J[i][a], jb = J[i][b];
+    J[i][a] = c * ja + s * jb;
+    J[i][b] = -s * ja + c * jb;
+  }
+}
+
+// Returns the number of steps, or -1 - steps when the subproblem has no
+// feasible point (it then ends at the last point reached); u (4) receives the
+// multipliers of rows lim0, lim1, ang_hi, ang_lo (layout of line_solve's u),
+// x the solution.
+template <typename T>
+ACOPF_HD inline int line_solve_exact(const LineQP<T>& P, T x[4], T u[4], int maxit = 32) {
+  // Q = L L' (Q is positive definite by construction of the record)
+  const T* q = P.q;
+  T l00 = sqrt(q[0]);
+  T l10 = q[1] / l00, l20 = q[2] / l00, l30 = q[3] / l00;
+  T l11 = sqrt(q[4] - l10 * l10);
+  T l21 = (q[5] - l20 * l10) / l11, l31 = (q[6] - l30 * l10) / l11;
+  T l22 = sqrt(q[7] - l20 * l20 - l21 * l21);
+  T l32 = (q[8] - l30 * l20 - l31 * l21) / l22;
+  T l33 = sqrt(q[9] - l30 * l30 - l31 * l31 - l32 * l32);
+  // J = L^-T (upper triangular): M = L^-1 by forward substitution, J = M'
+  T J[4][4];
+  {
+    T m00 = T(1) / l00, m11 = T(1) / l11, m22 = T(1) / l22, m33 = T(1) / l33;
+    T m10 = -l10 * m00 * m11;
+    T m21 = -l21 * m11 * m22;
+    T m20 = -(l20 * m00 + l21 * m10) * m22;
+    T m32 = -l32 * m22 * m33;
+    T m31 = -(l31 * m11 + l32 * m21) * m33;
+    T m30 = -(l30 * m00 + l31 * m10 + l32 * m20) * m33;
+    J[0][0] = m00; J[0][1] = m10; J[0][2] = m20; J[0][3] = m30;
+    J[1][0] = T(0); J[1][1] = m11; J[1][2] = m21; J[1][3] = m31;
+    J[2][0] = T(0); J[2][1] = T(0); J[2][2] = m22; J[2][3] = m32;
+    J[3][0] = T(0); J[3][1] = T(0); J[3][2] = T(0); J[3][3] = m33;
+  }
+  // unconstrained minimiser x = -J J' c
+  {
+    T t[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t[j] = J[0][j] * P.c[0] + J[1][j] * P.c[1] + J[2][j] * P.c[2] + J[3][j] * P.c[3];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = -(J[i][0] * t[0] + J[i][1] * t[1] + J[i][2] * t[2] + J[i][3] * t[3]);
+  }
+  T R[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) R[i][j] = T(0);
+  T ua[5] = {T(0), T(0), T(0), T(0), T(0)};  // multipliers of the active constraints (+ the one being added)
+  int act[4] = {-1, -1, -1, -1};
+  int nq = 0;
+  T cs = T(0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) cs = fmax(cs, fabs(P.c[i]));
+  const T eps = Eps<T>::v;
+  int steps = 0;
+  bool done = false, infeasible = false;
+  while (!done && steps < maxit) {
+    // most violated constraint, by its violation relative to its scale
+    T xs = fmax(fmax(fabs(x[0]), fabs(x[1])), fmax(fabs(x[2]), fabs(x[3])));
+    int p = -1;
+    T worst = T(0), sp = T(0);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      bool in = false;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) in = in || (a < nq && act[a] == k);
+      T n[4], b;
+      if (!gi_row(P, k, n, b) || in) continue;
+      T sk = n[0] * x[0] + n[1] * x[1] + n[2] * x[2] + n[3] * x[3] - b;
+      T nn = fabs(n[0]) + fabs(n[1]) + fabs(n[2]) + fabs(n[3]);
+      T v = -sk / (T(1) + fabs(b) + nn * xs);
+      if (v > worst) { worst = v; p = k; sp = sk; }
+    }
+    if (p < 0 || worst <= T(64) * eps) break;
+    T np[4], bp;
+    gi_row(P, p, np, bp);
+#pragma unroll
+    for (int a = 0; a < 5; ++a)
+      if (a == nq) ua[a] = T(0);
+    // add p, with partial steps that drop constraints, until it is active
+    for (int inner = 0; inner < 8 && steps < maxit; ++inner) {
+      ++steps;
+      T d[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) d[j] = J[0][j] * np[0] + J[1][j] * np[1] + J[2][j] * np[2] + J[3][j] * np[3];
+      // primal direction z = J2 d2, dual direction r = R^-1 d1
+      T z[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j >= nq)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) z[i] += J[i][j] * d[j];
+      T r[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+      for (int i = 3; i >= 0; --i) {
+        if (i >= nq) continue;
+        T sacc = d[i];
+#pragma unroll
+        for (int j = i + 1; j < 4; ++j)
+          if (j < nq) sacc -= R[i][j] * r[j];
+        r[i] = sacc / R[i][i];
+      }
+      // partial step: the active multiplier that reaches zero first
+      T t1 = T(0);
+      int kd = -1;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (j >= nq || !(r[j] > T(0))) continue;
+        T tj = ua[j] / r[j];
+        if (kd < 0 || tj < t1) { t1 = tj; kd = j; }
+      }
+      // full step: p becomes active
+      T zn = z[0] * np[0] + z[1] * np[1] + z[2] * np[2] + z[3] * np[3];
+      T dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + d[3] * d[3];
+      const bool full_ok = zn > T(64) * eps * dd;
+      T t2 = full_ok ? -sp / zn : T(0);
+      if (!full_ok && kd < 0) { done = infeasible = true; break; }  // no feasible point
+      const bool partial = kd >= 0 && (!full_ok || t1 < t2);
+      const T t = partial ? t1 : t2;
+      if (full_ok) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] += t * z[i];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < nq) ua[j] -= t * r[j];
+#pragma unroll
+      for (int a = 0; a < 5; ++a)
+        if (a == nq) ua[a] += t;
+      if (!partial) {
+        // add p: rotate d[j] (j > nq) into d[nq]; R's new column is d[0..nq]
+#pragma unroll
+        for (int j = 3; j >= 1; --j) {
+          if (j <= nq || d[j] == T(0)) continue;
+          T h = sqrt(d[j - 1] * d[j - 1] + d[j] * d[j]);
+          T c = d[j - 1] / h, s = d[j] / h;
+          d[j - 1] = h;
+          d[j] = T(0);
+          gi_rot_cols(J, j - 1, j, c, s);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (j == nq && i <= nq) R[i][j] = d[i];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+          if (a == nq) act[a] = p;
+        ++nq;
+        break;
+      }
+      // drop the constraint at position kd: remove its column of R and its
+      // multiplier (the entering one moves down with the others), then
+      // restore R's triangular form by rotations
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        if (j >= kd && j < nq - 1) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) R[i][j] = R[i][j + 1];
+          act[j] = act[j + 1];
+        }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j >= kd && j < nq) ua[j] = ua[j + 1];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (j == nq - 1) R[i][j] = T(0);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        if (j < kd || j >= nq - 1) continue;
+        T a0 = R[j][j], b0 = R[j + 1][j];
+        if (b0 == T(0)) continue;
+        T h = sqrt(a0 * a0 + b0 * b0);
+        T c = a0 / h, s = b0 / h;
+#pragma unroll
+        for (int col = 0; col < 4; ++col) {
+          if (col < j || col >= nq - 1) continue;
+          T ra = R[j][col], rb = R[j + 1][col];
+          R[j][col] = c * ra + s * rb;
+          R[j + 1][col] = -s * ra + c * rb;
+        }
+        gi_rot_cols(J, j, j + 1, c, s);
+      }
+      --nq;
+      sp = np[0] * x[0] + np[1] * x[1] + np[2] * x[2] + np[3] * x[3] - bp;
+    }
+  }
+  (void)cs;
+  if (sizeof(T) < sizeof(double)) {
+    // one step of iterative refinement on the final active set: residuals of
+    // stationarity (Qx + c - N u = 0) and of the active rows (N'x = b) in
+    // twice the working precision, the correction from the factors J and R
+    // (with dx = J y: R' y1 = r_b, y2 = (J'r_x)_2, R du = y1 - (J'r_x)_1)
+    T rx[4], rb[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      Dot2Acc<T> acc(-P.c[i]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc.add(-q[pk(i, j)], x[j]);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        if (a >= nq) continue;
+        T n[4], b;
+        gi_row(P, act[a], n, b);
+        acc.add(n[i], ua[a]);
+      }
+      rx[i] = acc.value();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (a >= nq) continue;
+      T n[4], b;
+      gi_row(P, act[a], n, b);
+      Dot2Acc<T> acc(b);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc.add(-n[j], x[j]);
+      rb[a] = acc.value();
+    }
+    T w[4], y[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = J[0][j] * rx[0] + J[1][j] * rx[1] + J[2][j] * rx[2] + J[3][j] * rx[3];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (i >= nq) {
+        y[i] = w[i];
+        continue;
+      }
+      T sacc = rb[i];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k < i) sacc -= R[k][i] * y[k];
+      y[i] = sacc / R[i][i];
+    }
+    T du[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+      if (i >= nq) continue;
+      T sacc = y[i] - w[i];
+#pragma unroll
+      for (int k = i + 1; k < 4; ++k)
+        if (k < nq) sacc -= R[i][k] * du[k];
+      du[i] = sacc / R[i][i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] += J[i][0] * y[0] + J[i][1] * y[1] + J[i][2] * y[2] + J[i][3] * y[3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+      if (a < nq) ua[a] += du[a];
+  }
+  // bounds hold to rounding; keep x inside the box exactly
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x[i] = clampv(x[i], P.lo[i], P.hi[i]);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) u[r] = T(0);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    if (a >= nq) continue;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (act[a] == 8 + r) u[r] = ua[a];
+  }
+  return infeasible ? -1 - steps : steps;
 }
 
 // row r of the ALM: h_r(x) (<= 0 when satisfied); rows 2, 3 are the angle rows

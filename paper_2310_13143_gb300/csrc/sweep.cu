@@ -45,7 +45,12 @@ struct SweepP {
   double rb_mu, rb_tau;
   int stages;     // FP32 sweep: 0 (branches read their records from global memory), 1 or 2 branch-tile buffers
   int profile;    // accumulate CTA 0's phase times into d.phase_ns
+  int smem_res;   // 1: residual maxima accumulated per CTA in shared memory (K <= kSmemResMax)
+  int line_exact; // FP64 sweep: 1 = line subproblems by the exact dual active-set method, 0 = ALM
 };
+
+// instances up to which the residual maxima are accumulated in shared memory
+constexpr int kSmemResMax = 1024;
 
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
@@ -60,30 +65,27 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
-// returns false (in every thread of the CTA) when this CTA gave up waiting or
-// another CTA reported that it did
-__device__ bool grid_barrier(unsigned* bar, int* err, long long spin_limit) {
+// Device-wide barrier on one arrival counter that only grows (it is zeroed
+// before every launch): at its n-th barrier a CTA adds 1 with release
+// semantics and waits, with acquire loads, until the counter reaches
+// n * gridDim.x.  One atomic per CTA and no reset, so the last CTA to arrive
+// releases the others by its own arrival.  epoch is the calling CTA's target
+// (held by thread 0).  Returns false (in every thread of the CTA) when this
+// CTA gave up waiting or another CTA reported that it did.
+__device__ bool grid_barrier(unsigned* count, unsigned& epoch, int* err, long long spin_limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    unsigned* count = bar;
-    unsigned* gen = bar + 1;
-    unsigned g0 = ld_acquire(gen);
+    epoch += gridDim.x;
     __threadfence();
-    unsigned arrived = atomicAdd(count, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
-      long long t0 = clock64();
-      while (ld_acquire(gen) == g0) {
-        if (clock64() - t0 > spin_limit) {
-          atomicExch(err, 1);
-          ok = 0;
-          break;
-        }
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+    long long t0 = clock64();
+    while ((int)(ld_acquire(count) - epoch) < 0) {
+      if (clock64() - t0 > spin_limit) {
+        atomicExch(err, 1);
+        ok = 0;
+        break;
       }
     }
     __threadfence();
@@ -149,6 +151,20 @@ __device__ __forceinline__ void tile_issue(const Dev& d, int l0, int n, V4<T>* s
 }
 
 // ------------------------------------------------------------- phases
+// eq. gen_kernel for generator g from its record chunks a = (f', f'', lp, up),
+// b = (lq, uq, rho, 0): clamp((rho z - lambda - f') / (f'' + rho)) and
+// clamp((rho z - lambda) / rho)
+template <typename T>
+__device__ __forceinline__ void gen_compute(const Dev& d, int g, const V4<T>& a, const V4<T>& b) {
+  V2<T> z = ((const V2<T>*)d.ZG)[g];
+  V2<T> lam = ((const V2<T>*)d.LG)[g];
+  T rho = b.z;
+  V2<T> x;
+  x.x = clampv(div_w(rho * z.x - lam.x - a.x, a.y + rho), a.z, a.w);
+  x.y = clampv(div_w(rho * z.y - lam.y, rho), b.x, b.y);
+  ((V2<T>*)d.XG)[g] = x;
+}
+
 template <typename T>
 __device__ __forceinline__ void gen_phase(const SweepP<T>& p, int g, float sc) {
   const Dev& d = p.d;
@@ -158,15 +174,37 @@ __device__ __forceinline__ void gen_phase(const SweepP<T>& p, int g, float sc) {
     b.z = (T)((double)b.z * (double)sc);
     R[d.G + g] = b;
   }
-  V2<T> z = ((const V2<T>*)d.ZG)[g];
-  V2<T> lam = ((const V2<T>*)d.LG)[g];
-  T rho = b.z;
-  // eq. gen_kernel: clamp((rho z - lambda - f') / (f'' + rho)) and clamp((rho z - lambda) / rho)
-  V2<T> x;
-  x.x = clampv(div_w(rho * z.x - lam.x - a.x, a.y + rho), a.z, a.w);
-  x.y = clampv(div_w(rho * z.y - lam.y, rho), b.x, b.y);
-  ((V2<T>*)d.XG)[g] = x;
+  gen_compute(d, g, a, b);
 }
+
+// the augmented Lagrangian as a call of its own in the FP64 sweep (see line_compute)
+template <typename T>
+__device__ __noinline__ void line_alm_call(const LineQP<T>& P, T* x, T* u, T beta, T tol, int outer, int newton) {
+  line_solve(P, x, u, beta, tol, outer, newton);
+}
+
+// How a line solve reads its branch's sweep record: value e (0..55) of the
+// layout in common.cuh, and again(e) for the values read a second time after
+// the solve.
+template <typename T>
+struct GRec {  // in global memory (stride L) or a shared-memory tile (stride TILE)
+  const T* rt;
+  int rstride;
+  __device__ __forceinline__ T operator()(int e) const { return rt[4 * (e >> 2) * rstride + (e & 3)]; }
+  // volatile: not held in registers across the solve
+  __device__ __forceinline__ T again(int e) const {
+    return ((const volatile T*)rt)[4 * (e >> 2) * rstride + (e & 3)];
+  }
+};
+template <typename T>
+struct RRec {  // held in registers for the whole sweep (every index is a constant after unrolling)
+  const V4<T>* r;
+  __device__ __forceinline__ T operator()(int e) const {
+    const V4<T>& v = r[e >> 2];
+    return (e & 3) == 0 ? v.x : (e & 3) == 1 ? v.y : (e & 3) == 2 ? v.z : v.w;
+  }
+  __device__ __forceinline__ T again(int e) const { return (*this)(e); }
+};
 
 // Residual balancing changed this branch's penalty by the factor sc:
 // Q = A'HA + rho (F'F + I) and c0 = gH + rho F'f0 change with rho.  The
@@ -200,18 +238,14 @@ __device__ __noinline__ T rb_rescale(const Dev& d, int l, float sc, V4<T>* rs, i
   return rn;
 }
 
-// One branch's line subproblem.  rs points at chunk 0 of the branch's record;
-// chunk c is at rs[c * rstride] (global memory: stride L; a shared-memory tile:
-// stride TILE).  Record values are read where they are used rather than
-// copied to registers, to keep the kernel's register count low.  z, lambda,
-// u and rho are passed in.
-template <typename T>
-__device__ __forceinline__ void line_compute(const SweepP<T>& p, int l, float sc, V4<T>* rs, int rstride,
-                                             V4<T> z0, V4<T> z1, V4<T> l0, V4<T> l1, V4<T> uu, T rho) {
+// One branch's line subproblem.  rec reads the branch's record (global
+// memory, a shared-memory tile or registers); values are read where they are
+// used rather than copied to registers, to keep the kernel's register count
+// low.  z, lambda, u and rho are passed in.
+template <typename T, typename Rec>
+__device__ __forceinline__ void line_compute(const SweepP<T>& p, int l, const Rec& rec, V4<T> z0, V4<T> z1, V4<T> l0,
+                                             V4<T> l1, V4<T> uu, T rho) {
   const Dev& d = p.d;
-  if (sc != 1.0f) rho = rb_rescale(d, l, sc, rs, rstride, rho);
-  const T* rt = (const T*)rs;
-  auto rec = [&](int e) -> T { return rt[4 * (e >> 2) * rstride + (e & 3)]; };
   // couplings: flows p_ij q_ij p_ji q_ji (F rows 0..3), voltages dbar 0..3
   const T zf[4] = {z0.x, z0.y, z1.x, z1.y}, lf[4] = {l0.x, l0.y, l1.x, l1.y};
   const T zv[4] = {z0.z, z0.w, z1.z, z1.w}, lv[4] = {l0.z, l0.w, l1.z, l1.w};
@@ -241,20 +275,35 @@ __device__ __forceinline__ void line_compute(const SweepP<T>& p, int l, float sc
   T x[4], u[4] = {uu.x, uu.y, uu.z, uu.w};
 #pragma unroll
   for (int i = 0; i < 4; ++i) x[i] = clampv(zv[i], P.lo[i], P.hi[i]);
-  T qd = fmax(fmax(P.q[0], P.q[4]), fmax(P.q[7], P.q[9]));
-  line_solve(P, x, u, p.beta_scale * qd, p.alm_tol, p.alm_outer, p.newton_max);
-  // flows at the solution; F and f0 are read again (volatile: not held in
-  // registers across the solve)
-  const volatile T* rv = rt;
+  const T beta = p.beta_scale * fmax(fmax(P.q[0], P.q[4]), fmax(P.q[7], P.q[9]));
+  if constexpr (sizeof(T) == 8) {
+    // FP64 sweep: the exact dual active-set method by default (the augmented
+    // Lagrangian, called out of line, for line_solver = 1 and for a
+    // subproblem with no feasible point: it treats the rows softly)
+    bool alm = !p.line_exact;
+    if (p.line_exact) {
+      const T u_in[4] = {u[0], u[1], u[2], u[3]};
+      if (line_solve_exact(P, x, u) < 0) {
+        alm = true;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          x[i] = clampv(zv[i], P.lo[i], P.hi[i]);
+          u[i] = u_in[i];
+        }
+      }
+    }
+    if (alm) line_alm_call(P, x, u, beta, p.alm_tol, p.alm_outer, p.newton_max);
+  } else {
+    // FP32 sweep: the augmented Lagrangian with refinement (Sec. IV-B)
+    line_solve(P, x, u, beta, p.alm_tol, p.alm_outer, p.newton_max);
+  }
+  // flows at the solution (F and f0 read again)
   T xf[4];
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
-    T s = rv[4 * ((26 + f) >> 2) * rstride + ((26 + f) & 3)];
+    T s = rec.again(26 + f);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = 10 + 4 * f + i;
-      s += rv[4 * (e >> 2) * rstride + (e & 3)] * x[i];
-    }
+    for (int i = 0; i < 4; ++i) s += rec.again(10 + 4 * f + i) * x[i];
     xf[f] = s;
   }
   V4<T>* X = (V4<T>*)d.X;
@@ -267,14 +316,55 @@ __device__ __forceinline__ void line_compute(const SweepP<T>& p, int l, float sc
   ((V4<T>*)d.U)[l] = ou;
 }
 
+// line update of branch l reading its record from global memory (rs, stride L)
+// or a shared-memory tile (stride TILE); applies a residual-balancing change
+// of its penalty first
+template <typename T>
+__device__ __forceinline__ void line_from(const SweepP<T>& p, int l, float sc, V4<T>* rs, int rstride, V4<T> z0,
+                                          V4<T> z1, V4<T> l0, V4<T> l1, V4<T> uu, T rho) {
+  if (sc != 1.0f) rho = rb_rescale(p.d, l, sc, rs, rstride, rho);
+  line_compute(p, l, GRec<T>{(const T*)rs, rstride}, z0, z1, l0, l1, uu, rho);
+}
 
 template <typename T>
 __device__ __forceinline__ void line_phase(const SweepP<T>& p, int l, float sc) {
   const Dev& d = p.d;
   const V4<T>* Z = (const V4<T>*)d.Z;
   const V4<T>* LM = (const V4<T>*)d.LAM;
-  line_compute(p, l, sc, (V4<T>*)d.lrec + l, d.L, Z[2 * l], Z[2 * l + 1], LM[2 * l], LM[2 * l + 1],
-               ((const V4<T>*)d.U)[l], ((const T*)d.trho_l)[l]);
+  line_from(p, l, sc, (V4<T>*)d.lrec + l, d.L, Z[2 * l], Z[2 * l + 1], LM[2 * l], LM[2 * l + 1],
+            ((const V4<T>*)d.U)[l], ((const T*)d.trho_l)[l]);
+}
+
+// Where the residual maxima of one iteration go: with acc set, per-instance
+// accumulators in the CTA's shared memory (flushed to the global slots by
+// res_flush once per iteration, so the number of global atomics per instance
+// is one per CTA, not one per warp task); otherwise the global slots of
+// iteration parity slot directly.
+struct ResDst {
+  unsigned long long* acc;  // shared [2][K] or null
+  unsigned long long* slots;
+  int K, slot;
+  __device__ __forceinline__ void put(int inst, double r, double s) const {
+    if (acc) {
+      if (r > 0.0) atomicMax(&acc[inst], (unsigned long long)__double_as_longlong(r));
+      if (s > 0.0) atomicMax(&acc[K + inst], (unsigned long long)__double_as_longlong(s));
+    } else {
+      if (r > 0.0) atomicMax(&slots[(slot * 2 + 0) * K + inst], (unsigned long long)__double_as_longlong(r));
+      if (s > 0.0) atomicMax(&slots[(slot * 2 + 1) * K + inst], (unsigned long long)__double_as_longlong(s));
+    }
+  }
+};
+
+// the CTA's shared-memory maxima into the global slots, and back to zero
+// (every thread of the CTA calls it after a __syncthreads)
+__device__ __forceinline__ void res_flush(const ResDst& o) {
+  for (int k = threadIdx.x; k < o.K; k += blockDim.x) {
+    const unsigned long long r = o.acc[k], s = o.acc[o.K + k];
+    if (r) atomicMax(&o.slots[(o.slot * 2 + 0) * o.K + k], r);
+    if (s) atomicMax(&o.slots[(o.slot * 2 + 1) * o.K + k], s);
+    o.acc[k] = 0ull;
+    o.acc[o.K + k] = 0ull;
+  }
 }
 
 // Warp-level max of the residuals over runs of lanes that hold the same
@@ -282,7 +372,7 @@ __device__ __forceinline__ void line_phase(const SweepP<T>& p, int l, float sc) 
 // shuffle-down reduction in the sweep precision, then one 64-bit atomicMax per
 // run and residual.  All 32 lanes must call it; lanes without a bus pass inst = -1.
 template <typename T>
-__device__ __forceinline__ void res_max2(unsigned long long* slots, int K, int slot, T r, T s, int inst) {
+__device__ __forceinline__ void res_max2(const ResDst& dst, T r, T s, int inst) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -297,17 +387,12 @@ __device__ __forceinline__ void res_max2(unsigned long long* slots, int K, int s
   }
   int kprev = __shfl_up_sync(FULL, inst, 1);
   bool leader = (lane == 0 || kprev != inst) && inst >= 0;
-  if (leader) {
-    double rd = (double)r, sd = (double)s;
-    if (rd > 0.0) atomicMax(&slots[(slot * 2 + 0) * K + inst], (unsigned long long)__double_as_longlong(rd));
-    if (sd > 0.0) atomicMax(&slots[(slot * 2 + 1) * K + inst], (unsigned long long)__double_as_longlong(sd));
-  }
+  if (leader) dst.put(inst, (double)r, (double)s);
 }
 
 // res_max2 for two tasks at once
 template <typename T>
-__device__ __forceinline__ void res_max2_pair(unsigned long long* slots, int K, int slot, T ra, T sa, int ka, T rb,
-                                              T sb, int kb) {
+__device__ __forceinline__ void res_max2_pair(const ResDst& dst, T ra, T sa, int ka, T rb, T sb, int kb) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -328,16 +413,8 @@ __device__ __forceinline__ void res_max2_pair(unsigned long long* slots, int K, 
     }
   }
   const int kpa = __shfl_up_sync(FULL, ka, 1), kpb = __shfl_up_sync(FULL, kb, 1);
-  if ((lane == 0 || kpa != ka) && ka >= 0) {
-    double rd = (double)ra, sd = (double)sa;
-    if (rd > 0.0) atomicMax(&slots[(slot * 2 + 0) * K + ka], (unsigned long long)__double_as_longlong(rd));
-    if (sd > 0.0) atomicMax(&slots[(slot * 2 + 1) * K + ka], (unsigned long long)__double_as_longlong(sd));
-  }
-  if ((lane == 0 || kpb != kb) && kb >= 0) {
-    double rd = (double)rb, sd = (double)sb;
-    if (rd > 0.0) atomicMax(&slots[(slot * 2 + 0) * K + kb], (unsigned long long)__double_as_longlong(rd));
-    if (sd > 0.0) atomicMax(&slots[(slot * 2 + 1) * K + kb], (unsigned long long)__double_as_longlong(sd));
-  }
+  if ((lane == 0 || kpa != ka) && ka >= 0) dst.put(ka, (double)ra, (double)sa);
+  if ((lane == 0 || kpb != kb) && kb >= 0) dst.put(kb, (double)rb, (double)sb);
 }
 
 // ---------------------------------------------------------- bus update
@@ -502,8 +579,36 @@ __device__ __forceinline__ void seg_scan2(int bus_a, T* Sa, int bus_b, T* Sb) {
   }
 }
 
-// the loads of one task of at most 32 entries: this lane's coupling, and for
-// the last lane of each bus its load and shunts (issued before any is used)
+// What of one task of at most 32 entries stays fixed during a sweep: this
+// lane's slot, whether it is the last lane of its bus, and for that lane the
+// bus's load and shunts
+template <typename T>
+struct TaskStatic {
+  Slot s;
+  bool last;
+  V4<T> br;
+  int isref;
+};
+
+template <typename T>
+__device__ __forceinline__ TaskStatic<T> task_static(const Dev& d, Slot s) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  TaskStatic<T> a;
+  a.s = s;
+  const int bnext = __shfl_down_sync(FULL, s.bus, 1);
+  a.last = s.bus >= 0 && (lane == 31 || bnext != s.bus);
+  a.br = {T(0), T(0), T(0), T(0)};
+  a.isref = 0;
+  if (a.last) {
+    a.br = ((const V4<T>*)d.brec)[s.bus];  // pdk qdk gs bs
+    a.isref = d.isref[s.bus];
+  }
+  return a;
+}
+
+// the loads of one task: this lane's coupling (lanes of finished instances
+// are emptied)
 template <typename T>
 struct TaskData {
   Slot s;
@@ -514,22 +619,19 @@ struct TaskData {
 };
 
 template <typename T>
-__device__ __forceinline__ TaskData<T> task_load(const Dev& d, Slot s, const int* s_done) {
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ TaskData<T> task_load(const Dev& d, const TaskStatic<T>& st, const int* s_done) {
   TaskData<T> a;
-  if (s.bus >= 0 && s_done[s.inst]) s.bus = s.inst = -1;
-  a.s = s;
-  const int bnext = __shfl_down_sync(FULL, s.bus, 1);
-  a.last = s.bus >= 0 && (lane == 31 || bnext != s.bus);
-  a.x = a.lm = a.zo = a.br = {T(0), T(0), T(0), T(0)};
-  a.r = T(1);
-  a.isref = 0;
-  if (s.bus >= 0) entry_load(d, s.code, a.x, a.lm, a.zo, a.r);
-  if (a.last) {
-    a.br = ((const V4<T>*)d.brec)[s.bus];  // pdk qdk gs bs
-    a.isref = d.isref[s.bus];
+  a.s = st.s;
+  a.last = st.last;
+  a.br = st.br;
+  a.isref = st.isref;
+  if (a.s.bus >= 0 && s_done[a.s.inst]) {
+    a.s.bus = a.s.inst = -1;
+    a.last = false;
   }
+  a.x = a.lm = a.zo = {T(0), T(0), T(0), T(0)};
+  a.r = T(1);
+  if (a.s.bus >= 0) entry_load(d, a.s.code, a.x, a.lm, a.zo, a.r);
   return a;
 }
 
@@ -538,7 +640,8 @@ __device__ __forceinline__ TaskData<T> task_load(const Dev& d, Slot s, const int
 // in one warp.  Tasks never share an entry or a bus, so the order of their
 // stores does not matter.  All 32 lanes call it.
 template <typename T>
-__device__ __forceinline__ void bus_task_pair(const Dev& d, const TaskData<T>& a, const TaskData<T>& b, int slot) {
+__device__ __forceinline__ void bus_task_pair(const Dev& d, const TaskData<T>& a, const TaskData<T>& b,
+                                              const ResDst& dst) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   T Sa[6] = {0, 0, 0, 0, 0, 0}, Sb[6] = {0, 0, 0, 0, 0, 0};
@@ -569,19 +672,19 @@ __device__ __forceinline__ void bus_task_pair(const Dev& d, const TaskData<T>& a
     if (!(rmb == rmb)) rmb = T(1e30);
     if (!(smb == smb)) smb = T(1e30);
   }
-  res_max2_pair(d.res_slots, d.K, slot, rma, sma, a.s.inst, rmb, smb, b.s.inst);
+  res_max2_pair(dst, rma, sma, a.s.inst, rmb, smb, b.s.inst);
 }
 
 // one bus with more than 32 entries (entries [q0, q1) of ent); lanes loop
 template <typename T>
-__device__ void bus_task_big(const SweepP<T>& p, int q0, int q1, int slot, const int* s_done) {
+__device__ void bus_task_big(const SweepP<T>& p, int q0, int q1, const ResDst& dst, const int* s_done) {
   const Dev& d = p.d;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int bus = d.ebus[q0];
   const int inst = d.bus_inst[bus];
   if (s_done[inst]) {
-    res_max2(d.res_slots, d.K, slot, T(0), T(0), -1);
+    res_max2(dst, T(0), T(0), -1);
     return;
   }
   T S[6] = {0, 0, 0, 0, 0, 0};
@@ -609,20 +712,28 @@ __device__ void bus_task_big(const SweepP<T>& p, int q0, int q1, int slot, const
   }
   if (!(rm == rm)) rm = T(1e30);
   if (!(sm == sm)) sm = T(1e30);
-  res_max2(d.res_slots, d.K, slot, rm, sm, inst);
+  res_max2(dst, rm, sm, inst);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sweep(SweepP<T> p) {
+// RES: every thread has at most one generator or branch and every warp at
+// most two bus tasks (checked by the launcher); their static data -- the
+// branch record, the generator record, instance ids, task slots and bus data
+// -- is loaded once, before the first iteration, and held in registers.
+template <typename T, bool RES>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && !RES) ? 2 : 1) k_sweep(SweepP<T> p) {
   const Dev& d = p.d;
-  extern __shared__ __align__(128) int s_done[];  // finished flags (K ints), penalty factors (K floats), tiles
+  // dynamic shared memory: residual accumulators (2K 64-bit, when smem_res),
+  // finished flags (K ints), penalty factors (K floats), branch tiles
+  extern __shared__ __align__(128) unsigned long long s_dyn[];
   const int K = d.K;
+  unsigned long long* s_acc = p.smem_res ? s_dyn : nullptr;
+  int* s_done = (int*)(s_dyn + (p.smem_res ? 2 * K : 0));
   float* s_scale = (float*)(s_done + K);
   const int nthreads = gridDim.x * blockDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   // FP32 sweep: branch tiles of blockDim.x are staged in one or two
   // shared-memory buffers (stages 1, 2), or read from global memory (stages 0)
-  const bool kTiled = sizeof(T) == 4 && p.stages > 0;
+  const bool kTiled = !RES && sizeof(T) == 4 && p.stages > 0;
   const int tile = blockDim.x;
   V4<T>* stage0 = (V4<T>*)(((uintptr_t)(s_scale + K) + 127) & ~(uintptr_t)127);
   const bool two = p.stages > 1;
@@ -637,8 +748,32 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sweep(SweepP<T>
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     s_done[k] = d.admm_done[k];
     s_scale[k] = 1.0f;
+    if (s_acc) s_acc[k] = s_acc[K + k] = 0ull;
   }
   __syncthreads();
+  // RES: this thread's phase-A item and its record, this warp's two bus tasks
+  const int lane = threadIdx.x & 31, wid = tid >> 5, nw = nthreads >> 5;
+  const Slot none = {-1, 0, -1};
+  int my_k = -1;
+  V4<T> rr[kRecChunks];
+  T my_rho = T(0);
+  TaskStatic<T> ta, tb;
+  if (RES) {
+    if (tid < d.G) {
+      my_k = d.gen_inst[tid];
+      rr[0] = ((const V4<T>*)d.grec)[tid];
+      rr[1] = ((const V4<T>*)d.grec)[d.G + tid];
+    } else if (tid < d.G + d.L) {
+      const int l = tid - d.G;
+      my_k = d.br_inst[l];
+#pragma unroll
+      for (int c = 0; c < kRecChunks; ++c) rr[c] = ((const V4<T>*)d.lrec)[(size_t)c * d.L + l];
+      my_rho = ((const T*)d.trho_l)[l];
+    }
+    ta = task_static<T>(d, wid < d.NT ? load_slot(d, wid, lane) : none);
+    tb = task_static<T>(d, wid + nw < d.NT ? load_slot(d, wid + nw, lane) : none);
+  }
+  unsigned epoch = 0;  // this CTA's barrier target
   int it = 0;
   bool aborted = false;
   unsigned long long tp0 = 0, tp1 = 0;
@@ -647,7 +782,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sweep(SweepP<T>
     const int slot = it & 1;
     if (prof) tp0 = gtimer();
     // phase A: generators then branches
-    if (!kTiled) {
+    if (RES) {
+      if (my_k >= 0 && !s_done[my_k]) {
+        if (tid < d.G) {
+          gen_compute(d, tid, rr[0], rr[1]);
+        } else {
+          const int l = tid - d.G;
+          const V4<T>* Z = (const V4<T>*)d.Z;
+          const V4<T>* LM = (const V4<T>*)d.LAM;
+          line_compute(p, l, RRec<T>{rr}, Z[2 * l], Z[2 * l + 1], LM[2 * l], LM[2 * l + 1], ((const V4<T>*)d.U)[l],
+                       my_rho);
+        }
+      }
+    } else if (!kTiled) {
       for (int u = tid; u < d.G + d.L; u += nthreads) {
         if (u < d.G) {
           int k = d.gen_inst[u];
@@ -697,7 +844,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sweep(SweepP<T>
           int k = d.br_inst[l];
           if (!s_done[k]) {
             const int j = threadIdx.x;
-            line_compute(p, l, s_scale[k], cur + j, tile, cur[14 * tile + 2 * j], cur[14 * tile + 2 * j + 1],
+            line_from(p, l, s_scale[k], cur + j, tile, cur[14 * tile + 2 * j], cur[14 * tile + 2 * j + 1],
                          cur[16 * tile + 2 * j], cur[16 * tile + 2 * j + 1], cur[18 * tile + j],
                          ((const T*)d.trho_l)[l]);
           }
@@ -721,31 +868,38 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sweep(SweepP<T>
         d.res_slots[(slot * 2 + 1) * K + k] = 0ull;
       }
     if (prof) { tp1 = gtimer(); atomicAdd(&d.phase_ns[0], tp1 - tp0); }
-    if (!grid_barrier(d.bar, d.err, p.spin_limit)) { aborted = true; break; }
+    if (!grid_barrier(d.bar, epoch, d.err, p.spin_limit)) { aborted = true; break; }
     if (prof) { tp0 = gtimer(); atomicAdd(&d.phase_ns[1], tp0 - tp1); }
+    const ResDst dst = {s_acc, d.res_slots, K, slot};
     // phase B: buses, in warp tasks of consecutive whole buses, two tasks at a
     // time (every entry belongs to one task, so the loads ahead never read
     // what the current tasks write); loop bounds are uniform per warp so that
     // all lanes reduce together
-    {
-      const int lane = threadIdx.x & 31, wid = tid >> 5, nw = nthreads >> 5;
-      const Slot none = {-1, 0, -1};
+    if (RES) {
+      if (wid < d.NT) bus_task_pair(d, task_load<T>(d, ta, s_done), task_load<T>(d, tb, s_done), dst);
+      for (int b = wid; b < d.NBIG; b += nw) bus_task_big(p, d.big[2 * b], d.big[2 * b + 1], dst, s_done);
+    } else {
       auto slot_at = [&](int t) { return t < d.NT ? load_slot(d, t, lane) : none; };
       // tasks wid, wid + nw, ... taken two at a time; the slots of the next
       // pair are in flight while a pair is solved
       Slot s1a = slot_at(wid + 2 * nw), s1b = slot_at(wid + 3 * nw);
-      TaskData<T> ca = task_load<T>(d, slot_at(wid), s_done), cb = task_load<T>(d, slot_at(wid + nw), s_done);
+      TaskData<T> ca = task_load<T>(d, task_static<T>(d, slot_at(wid)), s_done);
+      TaskData<T> cb = task_load<T>(d, task_static<T>(d, slot_at(wid + nw)), s_done);
       for (int t = wid; t < d.NT; t += 2 * nw) {
-        bus_task_pair(d, ca, cb, slot);
-        ca = task_load<T>(d, s1a, s_done);
-        cb = task_load<T>(d, s1b, s_done);
+        bus_task_pair(d, ca, cb, dst);
+        ca = task_load<T>(d, task_static<T>(d, s1a), s_done);
+        cb = task_load<T>(d, task_static<T>(d, s1b), s_done);
         s1a = slot_at(t + 4 * nw);
         s1b = slot_at(t + 5 * nw);
       }
-      for (int b = wid; b < d.NBIG; b += nw) bus_task_big(p, d.big[2 * b], d.big[2 * b + 1], slot, s_done);
+      for (int b = wid; b < d.NBIG; b += nw) bus_task_big(p, d.big[2 * b], d.big[2 * b + 1], dst, s_done);
+    }
+    if (s_acc) {
+      __syncthreads();
+      res_flush(dst);
     }
     if (prof) { tp1 = gtimer(); atomicAdd(&d.phase_ns[2], tp1 - tp0); }
-    if (!grid_barrier(d.bar, d.err, p.spin_limit)) { aborted = true; break; }
+    if (!grid_barrier(d.bar, epoch, d.err, p.spin_limit)) { aborted = true; break; }
     // residual test (Sec. IV-B) and residual balancing, evaluated identically by every CTA
     const bool rb_now = p.rb_period > 0 && ((it + 1) % p.rb_period) == 0;
     int all = 1;
@@ -855,10 +1009,60 @@ void launch_commit_rho(Ctx& c) {
 // for the FP32 sweep two branch-tile stages plus their mbarriers
 template <typename T>
 static size_t sweep_smem(int K, int threads, int stages) {
-  size_t b = (sizeof(int) + sizeof(float)) * (size_t)K;
+  size_t b = (sizeof(int) + sizeof(float)) * (size_t)K + (K <= kSmemResMax ? 16 * (size_t)K : 0);
   if (sizeof(T) == 4 && stages > 0)
     b = ((b + 127) & ~(size_t)127) + (size_t)stages * kTileV4 * threads * sizeof(V4<T>) + 16 + 128;
   return b;
+}
+
+// Launch shape of k_sweep<T>.  The resident form (sweep_stages 3) is used when
+// residual balancing is off and a co-resident grid gives every generator and
+// branch a thread of its own and every warp at most two bus tasks; otherwise
+// (and for sweep_stages 0-2) the streaming form, with enough CTAs for one pass
+// over the larger of the two phases, capped at the co-resident maximum.
+struct SweepShape {
+  void* fn;
+  int blocks;
+  size_t smem;
+};
+
+template <typename T>
+static acopf_status sweep_shape(Ctx& c, const SweepP<T>& p, SweepShape& sh) {
+  const Dev& d = c.d;
+  const int threads = c.block_threads;
+  if (c.sweep_stages == 3 && p.rb_period == 0) {
+    const size_t smem = sweep_smem<T>(d.K, threads, 0);
+    cudaFuncSetAttribute(k_sweep<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<T, true>, threads, smem);
+    if (c.ctas_per_sm > 0 && c.ctas_per_sm < per_sm) per_sm = c.ctas_per_sm;
+    const long wpb = threads / 32;
+    long need = ((long)d.G + d.L + threads - 1) / threads;
+    const long need_b = ((long)d.NT + 2 * wpb - 1) / (2 * wpb);
+    if (need_b > need) need = need_b;
+    if (need < 1) need = 1;
+    if (per_sm >= 1 && need <= (long)per_sm * c.num_sms) {
+      sh = {(void*)k_sweep<T, true>, (int)need, smem};
+      return ACOPF_OK;
+    }
+  }
+  const size_t smem = sweep_smem<T>(d.K, threads, p.stages);
+  cudaFuncSetAttribute(k_sweep<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<T, false>, threads, smem);
+  if (per_sm < 1) {
+    c.last_error = "sweep: the kernel does not fit on a multiprocessor";
+    return ACOPF_ECUDA;
+  }
+  if (c.ctas_per_sm > 0 && c.ctas_per_sm < per_sm) per_sm = c.ctas_per_sm;
+  long work = d.G + d.L;
+  if (d.B > work) work = d.B;
+  long need = (work + threads - 1) / threads;
+  long maxb = (long)per_sm * c.num_sms;
+  int blocks = (int)(need < maxb ? need : maxb);
+  if (blocks < 1) blocks = 1;
+  sh = {(void*)k_sweep<T, false>, blocks, smem};
+  return ACOPF_OK;
 }
 
 template <typename T>
@@ -878,24 +1082,14 @@ static acopf_status run_sweep(Ctx& c, const admm_options& o, int fixed_iters) {
   p.rb_period = o.rb_period;
   p.rb_mu = o.rb_mu;
   p.rb_tau = o.rb_tau;
-  p.stages = c.sweep_stages;
+  p.stages = c.sweep_stages == 3 ? 0 : c.sweep_stages;
   p.profile = c.profiling ? 1 : 0;
-  int threads = c.block_threads;
-  size_t smem = sweep_smem<T>(d.K, threads, c.sweep_stages);
-  cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<T>, threads, smem);
-  if (per_sm < 1) {
-    c.last_error = "sweep: the kernel does not fit on a multiprocessor";
-    return ACOPF_ECUDA;
-  }
-  if (c.ctas_per_sm > 0 && c.ctas_per_sm < per_sm) per_sm = c.ctas_per_sm;
-  long work = d.G + d.L;
-  if (d.B > work) work = d.B;
-  long need = (work + threads - 1) / threads;
-  long maxb = (long)per_sm * c.num_sms;
-  int blocks = (int)(need < maxb ? need : maxb);
-  if (blocks < 1) blocks = 1;
+  p.smem_res = d.K <= kSmemResMax;
+  p.line_exact = o.line_solver == 0;
+  const int threads = c.block_threads;
+  SweepShape sh;
+  acopf_status st = sweep_shape(c, p, sh);
+  if (st) return st;
   cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), c.stream);
   // inside a captured SQP iteration the error flag is not cleared: a barrier
   // time-out stays visible to the host and makes every later sweep return at
@@ -906,7 +1100,7 @@ static acopf_status run_sweep(Ctx& c, const admm_options& o, int fixed_iters) {
   void* args[] = {&p};
   const bool prof = c.profiling && !c.capturing;
   if (prof) cudaEventRecord(c.ev0, c.stream);
-  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_sweep<T>, dim3(blocks), dim3(threads), args, smem, c.stream);
+  cudaError_t e = cudaLaunchCooperativeKernel(sh.fn, dim3(sh.blocks), dim3(threads), args, sh.smem, c.stream);
   c.launches++;
   if (e != cudaSuccess) {
     c.last_error = std::string("sweep launch: ") + cudaGetErrorString(e);
@@ -1010,26 +1204,19 @@ acopf_status run_sweep_static(Ctx& c, const admm_options& o, int n, double* rs, 
   p.rb_period = o.rb_period;
   p.rb_mu = o.rb_mu;
   p.rb_tau = o.rb_tau;
-  p.stages = c.sweep_stages;
+  p.stages = c.sweep_stages == 3 ? 0 : c.sweep_stages;
   p.profile = 0;  // not timed: acopf_profile covers the handle's own sweeps only
-  int threads = c.block_threads;
-  size_t smem = sweep_smem<T>(d.K, threads, c.sweep_stages);
-  cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<T>, threads, smem) != cudaSuccess || per_sm < 1)
-    return ACOPF_ECUDA;
-  if (c.ctas_per_sm > 0 && c.ctas_per_sm < per_sm) per_sm = c.ctas_per_sm;
-  long work = d.G + d.L;
-  if (d.B > work) work = d.B;
-  long need = (work + threads - 1) / threads;
-  long maxb = (long)per_sm * c.num_sms;
-  int blocks = (int)(need < maxb ? need : maxb);
-  if (blocks < 1) blocks = 1;
+  p.smem_res = d.K <= kSmemResMax;
+  p.line_exact = o.line_solver == 0;
+  const int threads = c.block_threads;
+  SweepShape sh;
+  acopf_status st = sweep_shape(c, p, sh);
+  if (st) return st;
   // what must start at zero: barrier counters, error flag, residual slots
   cudaMemsetAsync(base, 0, kStaticHeader + sizeof(unsigned long long) * 4 * d.K, c.stream);
   k_static_init<<<nblk(d.K, 256), 256, 0, c.stream>>>(d, handle_done);
   void* args[] = {&p};
-  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_sweep<T>, dim3(blocks), dim3(threads), args, smem, c.stream);
+  cudaError_t e = cudaLaunchCooperativeKernel(sh.fn, dim3(sh.blocks), dim3(threads), args, sh.smem, c.stream);
   c.launches += 2;
   if (e != cudaSuccess) {
     c.last_error = std::string("admm_iterate_static launch: ") + cudaGetErrorString(e);
@@ -1062,7 +1249,7 @@ extern "C" acopf_status admm_iterate_static(acopf_handle h, int32_t n, const adm
   const admm_options& o = *ao;
   if (!(o.rho > 0) || !(o.eps >= 0) || !(o.eps_dual >= 0) || o.alm_max_outer < 1 || o.newton_max < 1 ||
       !(o.alm_beta > 0) || o.spin_limit < 1 || o.rb_period < 0 ||
-      (o.rb_period > 0 && (!(o.rb_mu > 1) || !(o.rb_tau > 1)))) {
+      (o.rb_period > 0 && (!(o.rb_mu > 1) || !(o.rb_tau > 1))) || o.line_solver < 0 || o.line_solver > 1) {
     c->last_error = "admm_iterate_static: admm options out of range";
     return ACOPF_EINVAL;
   }

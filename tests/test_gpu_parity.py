@@ -297,7 +297,7 @@ def test_autotune_applies_and_caches_a_shape(tmp_path):
     grids = [gg.grid_30bus()] * 4
     s = binding.Solver(grids, precision="mixed")
     shape, us = s.autotune(cache, iters=20)
-    assert shape[0] in (64, 128, 256) and shape[1] in (0, 1) and shape[2] in (0, 1, 2) and us > 0
+    assert shape[0] in (64, 128, 256) and shape[1] in (0, 1) and shape[2] in (0, 1, 2, 3) and us > 0
     import json
     entries = json.load(open(cache))
     assert len(entries) == 1 and entries[0]["block_threads"] == shape[0]
@@ -311,12 +311,12 @@ def test_autotune_applies_and_caches_a_shape(tmp_path):
 
 def test_mixed_sweep_launch_shapes_agree():
     """The FP32 sweep reads branch records from shared-memory tiles (one or two
-    buffers) or in place from global memory, with any CTA size: the same
-    arithmetic on the same values, so the state after a fixed number of
-    iterations must be identical."""
+    buffers), in place from global memory, or once into registers, with any
+    CTA size: the same arithmetic on the same values, so the state after a
+    fixed number of iterations must be identical."""
     grids = [gg.geometric_grid(118, seed=7), gg.grid_30bus(), gg.hub_grid(40)]
     ref = None
-    for bt, st in [(256, 1), (256, 0), (128, 2), (64, 0), (96, 1)]:
+    for bt, st in [(256, 1), (256, 0), (128, 2), (64, 0), (96, 1), (256, 3), (64, 3), (32, 3)]:
         s = binding.Solver(grids, precision="mixed")
         s.tune(bt, 0, st)
         s.build_qp(1.0, 2e4, True)
@@ -355,3 +355,23 @@ def test_linear_projection_matches_oracle(name):
         assert np.max(np.abs(E @ got - e)) <= 1e-6
         assert np.all(got >= lo - 1e-12) and np.all(got <= hi + 1e-12)
     s.close()
+
+
+def test_fp64_sweep_resident_records_agree():
+    """The FP64 sweep with records held in registers gives the same state as
+    with records read in place."""
+    grids = [gg.geometric_grid(118, seed=7), gg.grid_30bus(), gg.hub_grid(40)]
+    ref = None
+    for bt, st in [(256, 0), (256, 3), (64, 3)]:
+        s = binding.Solver(grids, precision="fp64")
+        s.tune(bt, 0, st)
+        s.build_qp(1.0, 2e4, True)
+        s.admm_iterate(25, binding.default_admm())
+        got = [s.get_admm_state(k) for k in range(len(grids))]
+        s.close()
+        if ref is None:
+            ref = got
+            continue
+        for a, b in zip(ref, got):
+            for key in a:
+                np.testing.assert_array_equal(a[key], b[key], err_msg=f"{key} threads {bt} mode {st}")

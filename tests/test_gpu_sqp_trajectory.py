@@ -1,0 +1,85 @@
+"""The GPU's SQP trajectory (Alg. 1) against the oracle's, iteration by
+iteration, in FP64: the same ADMM iteration counts and acceptance decisions,
+and the trust-region radius, step norm, actual and predicted merit
+reductions (Sec. II-C) to 1e-9 relative.
+
+The FP64 sweep solves every line subproblem exactly (dual active-set
+method), as the oracle does by enumeration, so the two follow the same path
+up to rounding.  A line subproblem with no feasible point inside its box has
+no unique answer -- the GPU treats its rows softly (the paper's augmented
+Lagrangian), the oracle takes its least-violating working set -- so rows are
+compared up to the first QP whose ADMM met one.
+
+The runs are the ones that make every branch of the trust-region rule occur
+on the 30-bus grid (rejections, boundary growth, the cap, interior steps,
+ared > 0 with pred <= 0), the default settings on the 30-bus grid, and the
+benchmark's settings on the 2,000-bus grid.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_13143_gb300 import binding, gridgen as gg
+from sqp_alg1 import alg1
+from test_sqp_control_pins import _classify
+
+pytestmark = pytest.mark.gpu
+
+RUNS = {
+    "syn30_A": (gg.grid_30bus, dict(delta0=0.5, delta_max=0.5, max_iter=20, mu=1e2, eps=1e-4, max_sqp=25)),
+    "syn30_B": (gg.grid_30bus, dict(delta0=0.25, delta_max=0.5, max_iter=60, mu=1e5, eps=1e-4, max_sqp=25)),
+    "syn30_default": (gg.grid_30bus, dict(max_sqp=30)),
+    "syn2000_bench": (gg.grid_2000bus, dict(tol=1e-4, max_sqp=20, eps=1e-3, max_iter=1000, rho=2e4)),
+}
+# branches of the trust-region rule the compared rows must contain
+NEED = {"syn30_A": ("reject", "grow", "cap", "interior", "ared_pos_pred_nonpos"),
+        "syn30_B": ("reject", "grow", "cap", "interior")}
+
+
+def _gpu_opts(o: oracle.SqpOptions):
+    return binding.default_sqp(mu=o.mu, tol=o.tol, step_tol=o.step_tol, delta0=o.delta0, delta_max=o.delta_max,
+                               delta_min=o.delta_min, max_sqp=o.max_sqp,
+                               admm=dict(rho=o.rho, eps=o.eps, eps_dual=0.0, max_iter=o.max_iter,
+                                         warm=o.warm_lambda))
+
+
+@pytest.mark.parametrize("name", list(RUNS))
+def test_sqp_history_matches_oracle(name):
+    make, run = RUNS[name]
+    g = make()
+    o = oracle.SqpOptions(**run)
+    m = oracle.Model(g)
+    line_fail = []
+    want = alg1(m, o, line_fail)
+    np.testing.assert_array_equal(want, m.sqp(o)["hist"])  # the driver is the oracle's own loop
+    s = binding.Solver(g, precision="fp64")
+    s.sqp_solve(_gpu_opts(o))
+    got = s.get_history(0)
+    res = s.get_residuals(0)
+    s.close()
+    bad = [k for k, n in enumerate(line_fail) if n > 0]
+    n = bad[0] if bad else len(want)
+    if not bad:
+        assert res["sqp_iter"] == len(want) == len(got), (res["sqp_iter"], len(want))
+    assert n >= min(len(want), 15), n
+    got, want = got[:n], want[:n]
+    for k in NEED.get(name, ()):
+        assert _classify(want, o.delta0, o.delta_max)[k].any(), f"compared rows do not exercise '{k}'"
+    # ADMM iterations per QP and acceptance decisions: identical
+    np.testing.assert_array_equal(got[:, 3], want[:, 3])
+    np.testing.assert_array_equal(got[:, 6], want[:, 6])
+    # trust radius after the update and step norm: relative 1e-9
+    np.testing.assert_allclose(got[:, 7], want[:, 7], rtol=1e-9, atol=0)
+    np.testing.assert_allclose(got[:, 8], want[:, 8], rtol=1e-9, atol=1e-13)
+    # merit reductions: relative 1e-9 of the reduction, or of the merit value's
+    # rounding level (1e-12 of the objective) where the reduction itself is tiny
+    for col in (9, 10):
+        tol = 1e-9 * np.abs(want[:, col]) + 1e-12 * np.abs(want[:, 0])
+        assert (np.abs(got[:, col] - want[:, col]) <= tol).all(), (col, got[:, col], want[:, col])
+    # objective, primal and dual measures after every iteration
+    np.testing.assert_allclose(got[:, 0], want[:, 0], rtol=1e-10)
+    acc = want[:, 6] > 0
+    np.testing.assert_allclose(got[acc, 1], want[acc, 1], rtol=1e-6, atol=1e-10)
+    np.testing.assert_allclose(got[acc, 2], want[acc, 2], rtol=1e-6, atol=1e-10)
+    if not bad:
+        assert res["result"] == m.sqp(o)["status"]
