@@ -37,14 +37,24 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def sweep_bytes_per_iter(B, L, G, tbytes):
-    """Bytes the fused sweep must move per ADMM iteration with its state in
-    memory: phase A reads the 56-value
-    line record, z, lambda, the ALM multipliers and rho and writes x and the
-    multipliers; generators read 8 + 4 values and write 2; phase B reads
-    x, lambda, old z and rho per branch end and writes z and lambda, and
-    does the same for generators; buses read 4 values and write 4; plus the
-    32-bit CSR/instance indices."""
+def alg_bytes_per_iter(B, L, G, wbytes):
+    """Algorithmic bytes one ADMM iteration of Alg. 2 must move with its
+    state in memory, per the scope table's count: 8 words per coupling
+    (component side: read z, lambda, write x; bus side: read x, lambda, old
+    z, write z, lambda), 40 words of static QP data per branch, 8 per
+    generator, 4 per bus, and a 4-byte CSR index per branch end and per
+    generator.  Words in the sweep precision (wbytes)."""
+    C = 8 * L + 2 * G
+    return (8 * C + 40 * L + 8 * G + 4 * B) * wbytes + 4 * (2 * L + G)
+
+
+def layout_bytes_per_iter(B, L, G, tbytes):
+    """Bytes this implementation's layout moves per ADMM iteration: phase A
+    reads the 56-value line record, z, lambda, the line-limit multipliers
+    and rho and writes x and the multipliers; generators read 8 + 4 values
+    and write 2; phase B reads x, lambda, old z and rho per branch end and
+    writes z and lambda, and does the same for generators; buses read 4
+    values and write 4; plus the 32-bit CSR/instance indices."""
     line_a = L * (56 + 8 + 8 + 4 + 1 + 8 + 4) * tbytes
     gen_a = G * (8 + 2 + 2 + 2) * tbytes
     ends_b = 2 * L * (4 + 4 + 4 + 1 + 4 + 4) * tbytes
@@ -52,6 +62,24 @@ def sweep_bytes_per_iter(B, L, G, tbytes):
     bus_b = B * (4 + 2 + 2) * tbytes
     idx = 4 * (2 * L + 2 * (B + 1) + B + L + G)
     return line_a + gen_a + ends_b + gens_b + bus_b + idx
+
+
+def roofline(B, L, G, wbytes, iters_per_launch, avg_launch_ms, traffic, kernel):
+    """Roofline of the sweep from CUDA-event launch times: algorithmic bytes
+    per launch / launch time against the measured HBM copy bandwidth; the
+    layout's own bytes are reported beside it."""
+    hbm, which = _peaks()
+    alg = alg_bytes_per_iter(B, L, G, wbytes)
+    lay = layout_bytes_per_iter(B, L, G, wbytes)
+    t = avg_launch_ms / 1e3
+    achieved = alg * iters_per_launch / t / 1e9 if t > 0 else 0.0
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic, "traffic_unit": "bytes per launch", "peak_source": which, "kernel": kernel,
+            "bytes_per_iter": alg, "bytes_model": "algorithmic (8 words/coupling, 40/branch, 8/gen, 4/bus, "
+                                                  "4 B index per branch end and generator)",
+            "layout_bytes_per_iter": lay,
+            "layout_frac": (lay * iters_per_launch / t / 1e9) / hbm if t > 0 else 0.0,
+            "iters_per_launch": iters_per_launch, "avg_launch_ms": avg_launch_ms}
 
 
 class Clocks:
@@ -113,8 +141,8 @@ def solver_options(binding, precision):
 
 def headline_config(grid, precision, world):
     """The workload of the headline line; the reference arm reports the same."""
-    return {"workload": f"synthetic 2000-bus grid ({grid.nbranch} branches, {grid.ngen} generators), "
-                        f"one full SQP-ADMM solve per step from a flat start to 1e-4 primal and dual "
+    return {"workload": f"synthetic 2000-bus grid ({grid.nbranch} branches, {grid.ngen} generators, voltage band "
+                        f"[0.9, 1.1]), one full SQP-ADMM solve per step from a flat start to 1e-4 primal and dual "
                         f"infeasibility; "
                         + ("FP32 ADMM sweep, FP64 build, residual norms, acceptance and iterate"
                            if precision == "mixed" else "FP64 throughout"),
@@ -247,13 +275,12 @@ def run_gpu(args, rank, world, local_rank):
     total_s, conv_all, iters_all = combine_ranks(m["total_s"], m["conv"], m["admm_iters"], world, dev)
     if rank != 0:
         return None
-    hbm, which = _peaks()
-    tb = 4 if args.precision == "mixed" else 8
-    bpi = sweep_bytes_per_iter(grid.nbus, grid.nbranch, grid.ngen, tb)
+    wb = 4 if args.precision == "mixed" else 8
     prof = m["prof"]
     avg_ms = prof["sweep_ms"] / max(prof["sweeps"], 1)
     iters_per_launch = prof["admm_iters"] / max(prof["sweeps"], 1)
-    achieved = bpi * iters_per_launch / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+    kernel = "k_sweep<float>" if args.precision == "mixed" else "k_sweep<double>"
+    traffic = measured_traffic("syn2000", iters_per_launch) if args.precision == "mixed" and world == 1 else None
     last = m["last"]
     out = {
         "metric": METRIC,
@@ -276,13 +303,7 @@ def run_gpu(args, rank, world, local_rank):
         "objective_last": m["obj"],
         "primal_last": last["primal"],
         "dual_last": last["dual"],
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm,
-                     "traffic": (measured_traffic("syn2000", iters_per_launch)
-                                 if args.precision == "mixed" and world == 1 else None),
-                     "traffic_unit": "bytes per launch", "peak_source": which,
-                     "kernel": "k_sweep<float>" if args.precision == "mixed" else "k_sweep<double>",
-                     "bytes_per_iter": bpi, "iters_per_launch": iters_per_launch, "avg_launch_ms": avg_ms},
+        "roofline": roofline(grid.nbus, grid.nbranch, grid.ngen, wb, iters_per_launch, avg_ms, traffic, kernel),
         "gpu_launches": m["launches"],
         "clocks": m["clocks"],
         "launch_shape": m["launch_shape"],
@@ -296,6 +317,7 @@ def run_gpu(args, rank, world, local_rank):
         out["e2e"] = {"value": m["e2e_conv"] / m["e2e_s"] if m["e2e_s"] > 0 else 0.0, "unit": "solves/s",
                       "h2d_bytes_per_step": 2 * 8 * grid.nbus,
                       "d2h_bytes_per_step": 8 * (2 * grid.ngen + 2 * grid.nbus + 2 * grid.nbranch + 1) + 88}
+    summary = {}
     if plain is not None:
         ps = plain["total_s"]
         nst = max(2, args.steps // 2)
@@ -303,22 +325,59 @@ def run_gpu(args, rank, world, local_rank):
                              "ms_per_step": 1e3 * ps / nst, "admm_iter_per_s": plain["admm_iters"] / ps,
                              "objective": plain["obj"], "objective_rel_diff_vs_mixed": abs(plain["obj"] - m["obj"]) / abs(plain["obj"]),
                              "avg_sweep_launch_ms": plain["prof"]["sweep_ms"] / max(plain["prof"]["sweeps"], 1)}
+        summary["plain_fp64_solves_s"] = round(out["plain_fp64"]["value"], 3)
     if world == 1 and not args.no_rho_sweep:
         out["rho_sweep"] = rho_sweep(grid, args.precision)
+        summary["rho_sweep_solves_s"] = {f"{r['rho']:g}": round(r["solves_per_s"], 2) for r in out["rho_sweep"]}
+    if world == 1 and not args.no_learned:
+        lw = learned_warm_start(args)
+        out["learned_warm_start"] = lw
+        summary["learned"] = {"cold_s": round(lw["cold"]["seconds"], 3), "warm_s": round(lw["warm"]["seconds"], 3),
+                              "speedup": round(lw["speedup_wall"], 2), "admm_ratio": round(lw["admm_iter_ratio"], 3),
+                              "warm_conv": lw["warm"]["converged"], "of": lw["held_out"],
+                              "gemm_frac": round(lw["tensor_gemm"]["frac"], 3)}
+        if "rho_effect" in lw:
+            summary["learned"]["rho_effect"] = lw["rho_effect"]
     if world == 1 and not args.no_batched:
         bgrids = workload_grids("batched")
-        out["batched_sweep"] = sweep_only(bgrids, args.precision, 50, 3, 1, workload="batched")
-        out["batched_sweep"]["workload"] = ("256 correlated load scenarios of the 2,000-bus grid + 64 grids of "
-                                            "118-10,000 buses (log-uniform), one persistent launch, ADMM sweep only")
-        out["batched_solve"] = batched_solve(bgrids)
-    if world == 1 and not args.no_learned:
-        out["learned_warm_start"] = learned_warm_start(args)
+        bs = sweep_only(bgrids, args.precision, 50, 3, 1, workload="batched")
+        bs["workload"] = ("256 correlated load scenarios of the 2,000-bus grid + 64 grids of 118-10,000 buses "
+                          "(log-uniform), one persistent launch, ADMM sweep only")
+        out["batched_sweep"] = bs
+        bsol = batched_solve(bgrids)
+        out["batched_solve"] = bsol
+        summary["batched_sweep"] = {"us_iter": round(bs["us_per_iter"], 1), "frac": round(bs["roofline"]["frac"], 3),
+                                    "layout_frac": round(bs["roofline"]["layout_frac"], 3)}
+        summary["batched_solve"] = {"solves_s": round(bsol["value"], 1), "conv": bsol["converged"],
+                                    "of": bsol["instances"], "s": round(bsol["seconds"], 3),
+                                    "plain_est_s": round(bsol["plain_fp64_sample"]["estimated_seconds_all"], 1),
+                                    "vs_plain": round(bsol["batched_vs_plain"], 1),
+                                    "MB": round(bsol["device_bytes"] / 2 ** 20)}
+        if world == 1 and not args.no_cpu_baseline:
+            cb3 = cpu_batched_leg(bgrids)
+            out["cpu_batched"] = cb3
+            summary["cpu_batched"] = {"solves_s": round(cb3["value"], 3), "cores": cb3["cores"]}
     if world == 1 and not args.no_large:
-        out["large_70k_x16"] = sweep_only(workload_grids("syn70k_x16"), "mixed", 30, 2, 1)
-        out["large_70k_x16"]["workload"] = ("16 correlated load scenarios of a 70,000-bus grid (90,000 branches, "
-                                            "10,000 generators) in one persistent launch, ADMM sweep only")
+        big = workload_grids("syn70k_x16")
+        lg = sweep_only(big, "mixed", 30, 2, 1)
+        lg["workload"] = ("16 correlated load scenarios of a 70,000-bus grid (90,000 branches, 10,000 generators) "
+                          "in one persistent launch, ADMM sweep only")
+        out["large_70k_x16"] = lg
+        summary["large_70k_x16"] = {"us_iter": round(lg["us_per_iter"], 1), "frac": round(lg["roofline"]["frac"], 3),
+                                    "MB": round(lg["device_bytes"] / 2 ** 20)}
+        if not args.no_large_solve:
+            ls = large_solve(big)
+            out["large_70k_solve"] = ls
+            summary["large_70k_solve"] = ls.get("summary", {})
+        if not args.no_cpu_baseline:
+            cl = cpu_large_leg(big[0])
+            out["cpu_large"] = cl
+            summary["cpu_large_iter_s"] = round(cl["admm_iter_per_s"], 2)
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(grid, iters_all / max(args.steps, 1), args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(grid)
+    # the figures above that the end of the line must carry (it is what a
+    # truncated record keeps): compact, last
+    out["summary"] = summary
     return out
 
 
@@ -354,17 +413,20 @@ def rho_sweep(grid, precision, rhos=(2e3, 5e3, 1e4, 2e4, 5e4), reps=3):
     return rows
 
 
-def batched_solve(grids, plain_sample=8):
+def batched_solve(grids, nscen=256, stride=10):
     """The uneven 320-instance batch solved to the end: every instance in one
     handle (launch shape from the autotuner, SQP loop replayed from a CUDA
-    graph), against a plain sample of the same instances solved one at a
-    time, cold, in FP64."""
+    graph), against the plain path -- one instance at a time, cold, FP64 --
+    on every stride-th instance of the same batch (scenarios and uneven grids
+    alike).  The plain time of the whole batch is estimated from that sample
+    per kind (count x mean time); the comparison is reported as an estimate."""
     import torch
 
     from paper_2310_13143_gb300 import binding
 
     opts = solver_options(binding, "mixed")
     stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     s = binding.Solver(grids, precision="mixed")
     s.set_stream(stream.cuda_stream)
@@ -382,10 +444,11 @@ def batched_solve(grids, plain_sample=8):
     rs = [s.get_residuals(k) for k in range(len(grids))]
     ok = [r["result_name"] == "converged" and r["primal"] <= 1e-4 and r["dual"] <= 1e-4 for r in rs]
     s.close()
-    # plain: a sample of the same instances, one handle each, cold, FP64
-    idx = list(range(0, len(grids), max(1, len(grids) // plain_sample)))[:plain_sample]
-    pt, pconv = 0.0, 0
+    # plain: one handle per sampled instance, cold, FP64
+    idx = list(range(0, len(grids), stride))
     popts = solver_options(binding, "fp64")
+    times = {"scenario": [], "uneven": []}
+    pconv = 0
     for i in idx:
         p = binding.Solver([grids[i]], precision="fp64")
         p.set_stream(stream.cuda_stream)
@@ -394,28 +457,33 @@ def batched_solve(grids, plain_sample=8):
         p.sqp_solve(popts)
         b.record(stream)
         torch.cuda.synchronize()
-        pt += a.elapsed_time(b) / 1e3
+        times["scenario" if i < nscen else "uneven"].append(a.elapsed_time(b) / 1e3)
         r = p.get_residuals(0)
         pconv += int(r["result_name"] == "converged" and r["primal"] <= 1e-4 and r["dual"] <= 1e-4)
         p.close()
-    sizes = [grids[i].nbus for i in idx]
+    counts = {"scenario": nscen, "uneven": len(grids) - nscen}
+    est = sum(counts[k] * (sum(v) / len(v)) for k, v in times.items() if v)
+    pt = sum(sum(v) for v in times.values())
     return {"instances": len(grids), "converged": int(sum(ok)), "seconds": t,
             "value": sum(ok) / t, "unit": "solves/s",
             "instances_per_s": len(grids) / t,
             "sqp_iters_max": max(r["sqp_iter"] for r in rs),
             "admm_iters_mean": float(sum(r["admm_iter"] for r in rs) / len(rs)),
+            "converged_scenarios": int(sum(ok[:nscen])), "converged_uneven": int(sum(ok[nscen:])),
             "launch_shape": {"block_threads": shape[0], "ctas_per_sm": shape[1], "stages": shape[2],
                              "tuned_us_per_iter": tune_us},
             "device_bytes": int(footprint),
-            "plain_fp64_sample": {"instances": len(idx), "buses": sizes, "converged": pconv, "seconds": pt,
+            "plain_fp64_sample": {"instances": len(idx), "stride": stride, "converged": pconv, "seconds": pt,
+                                  "mean_seconds": {k: (sum(v) / len(v) if v else None) for k, v in times.items()},
                                   "value": pconv / pt if pt > 0 else 0.0, "unit": "solves/s",
-                                  "instances_per_s": len(idx) / pt if pt > 0 else 0.0},
-            "batched_vs_plain_instances_per_s": (len(grids) / t) / (len(idx) / pt) if pt > 0 else None,
+                                  "estimated_seconds_all": est,
+                                  "estimate": "per kind: instances in the batch x mean sampled plain time"},
+            "batched_vs_plain": est / t if t > 0 else None,
             "workload": "256 correlated load scenarios of the 2,000-bus grid + 64 grids of 118-10,000 buses, "
                         f"one handle, SQP to 1e-4 (max {MAX_SQP} SQP iterations, 1,000 ADMM iterations per QP)"}
 
 
-def learned_warm_start(args, ntrain=4096, ntest=512, steps=6000, batch=256, lr=3e-3):
+def learned_warm_start(args, ntrain=4096, ntest=512, steps=6000, batch=256, lr=3e-3, rho_steps=1500, rho_lr=1e-3):
     """The learned warm start: the network trained on cold solves of sampled
     loads of the 2,000-bus grid and judged on held-out scenarios against
     cold starts of the same scenarios."""
@@ -440,8 +508,18 @@ def learned_warm_start(args, ntrain=4096, ntest=512, steps=6000, batch=256, lr=3
     t0 = time.perf_counter()
     losses = ws.train(net, Xd, Td, ntrain, steps=steps, batch=batch, lr=lr, seed=1004, schedule="cos")
     t_train = time.perf_counter() - t0
-    test = scen[ntrain:]
     stream = torch.cuda.Stream()
+    # per-component penalties (form 4): targets from solves started at the
+    # network's own predictions under candidate factors, then fine-tuning
+    t0 = time.perf_counter()
+    pick, cand = ws.rho_targets(scen[:ntrain], net, Xd, T, opts, stream_ptr=stream.cuda_stream)
+    t_rho_data = time.perf_counter() - t0
+    Td = torch.from_numpy(T).cuda()
+    net.fit_standardiser(Xd.data_ptr(), Td.data_ptr(), ntrain)
+    t0 = time.perf_counter()
+    ws.train(net, Xd, Td, ntrain, steps=rho_steps, batch=batch, lr=rho_lr, seed=1005, schedule="cos")
+    t_rho_train = time.perf_counter() - t0
+    test = scen[ntrain:]
     res = {}
     # cold: one handle, every held-out scenario from a flat start
     s = binding.Solver(test, precision="mixed")
@@ -469,6 +547,18 @@ def learned_warm_start(args, ntrain=4096, ntest=512, steps=6000, batch=256, lr=3
     t_warm = time.perf_counter() - t0
     s.close()
     res["warm"] = {"seconds": t_warm, "rs": rs, "obj": np.array(ob), "fallback": len(failed)}
+    # the same with the predicted per-component penalties applied
+    s = binding.Solver(test, precision="mixed")
+    s.set_stream(stream.cuda_stream)
+    s.sqp_solve_graph(opts, check_every=2)  # warm-up of the handle (graph capture)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rs, ob, failed = ws.solve_warm_with_fallback(s, test, net, Xd[ntrain:], opts, stream_ptr=stream.cuda_stream,
+                                                 use_rho=True)
+    torch.cuda.synchronize()
+    t_warm_rho = time.perf_counter() - t0
+    s.close()
+    res["warm_rho"] = {"seconds": t_warm_rho, "rs": rs, "obj": np.array(ob), "fallback": len(failed)}
     # the paper's linear feasibility projection (eq. linfeas) of the predicted
     # starts before the solve: its cost and its effect on the iterations
     s = binding.Solver(test, precision="mixed")
@@ -497,9 +587,15 @@ def learned_warm_start(args, ntrain=4096, ntest=512, steps=6000, batch=256, lr=3
     net.close()
     okc = res["cold"]["obj"]
     rel = np.abs(res["warm"]["obj"] - okc) / np.abs(okc)
+    rel_rho = np.abs(res["warm_rho"]["obj"] - okc) / np.abs(okc)
     for m in res:
         res[m].pop("obj")
         res[m]["solves_per_s"] = res[m]["converged"] / res[m]["seconds"]
+    chosen = np.bincount(pick, minlength=len(ws.RHO_CHOICES))
+    rho_effect = {"admm_ratio": round(res["warm_rho"]["admm_iters_mean"] / res["warm"]["admm_iters_mean"], 3),
+                  "sqp": [round(res["warm"]["sqp_iters_mean"], 2), round(res["warm_rho"]["sqp_iters_mean"], 2)],
+                  "wall_ratio": round(res["warm_rho"]["seconds"] / res["warm"]["seconds"], 3),
+                  "conv": res["warm_rho"]["converged"]}
     res["cold"]["timing"] = "host wall clock of sqp_solve_graph on a prepared handle"
     res["warm"]["timing"] = ("host wall clock of inference, scatter and sqp_solve_graph on a prepared handle, plus "
                              "the cold fallback (new handle) of instances that failed the convergence test")
@@ -507,8 +603,16 @@ def learned_warm_start(args, ntrain=4096, ntest=512, steps=6000, batch=256, lr=3
             "lr": f"{lr} with cosine decay to 0 (Adam)",
             "data_seconds": t_data, "train_seconds": t_train, "data_converged": int(conv.sum()),
             "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-10:].mean()),
-            "cold": res["cold"], "warm": res["warm"], "warm_projected_first": projected,
+            "cold": res["cold"], "warm": res["warm"], "warm_rho": res["warm_rho"], "warm_projected_first": projected,
+            "penalty_targets": {"choices_branch_gen": [list(c) for c in ws.RHO_CHOICES],
+                                "chosen": chosen.tolist(), "data_seconds": t_rho_data,
+                                "train_seconds": t_rho_train, "train_steps": rho_steps,
+                                "rule": "per scenario, the candidate (branch, generator) penalty factors whose solve from "
+                                        "the network's predicted start converges in the fewest ADMM iterations"},
+            "rho_effect": rho_effect,
+            "objective_rel_diff_max_with_rho": float(rel_rho.max()),
             "speedup_wall": res["cold"]["seconds"] / res["warm"]["seconds"],
+            "speedup_wall_with_rho": res["cold"]["seconds"] / res["warm_rho"]["seconds"],
             "admm_iter_ratio": res["warm"]["admm_iters_mean"] / res["cold"]["admm_iters_mean"],
             "objective_rel_diff_max": float(rel.max()), "objective_rel_diff_median": float(np.median(rel)),
             "tensor_gemm": gemm_roofline()}
@@ -581,6 +685,40 @@ def mlp_train_steps(steps, warmup, batch=256, dims=(4000, 512, 512, 512, 46504),
             "effective_tflop_s": (fwd + bwd) / (ms * 1e-3) / 1e12}
 
 
+def large_solve(grids, tol=1e-3, max_iter=1000):
+    """The 70,000-bus workload solved by SQP on the mixed-precision path, all
+    scenarios in one handle (graph loop), to the tolerance the paper uses on
+    its large cases (1e-3, Sec. V-A, Table II), cold start."""
+    import torch
+
+    from paper_2310_13143_gb300 import binding
+
+    stream = torch.cuda.Stream()
+    s = binding.Solver(grids, precision="mixed")
+    s.set_stream(stream.cuda_stream)
+    s.autotune(os.path.join(tempfile.gettempdir(), "acopf_tune_cache.json"), iters=30)
+    opts = binding.default_sqp(tol=tol, max_sqp=MAX_SQP, admm=dict(rho=2e4, max_iter=max_iter, eps=1e-3,
+                                                                   eps_dual=5e-3))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.sqp_solve_graph(opts, check_every=2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    rs = [s.get_residuals(k) for k in range(len(grids))]
+    s.close()
+    ok = [r["result_name"] == "converged" and r["primal"] <= tol and r["dual"] <= tol for r in rs]
+    primal = sorted(r["primal"] for r in rs)
+    out = {"instances": len(grids), "tolerance": tol, "converged": int(sum(ok)), "seconds": t,
+           "sqp_iters": [r["sqp_iter"] for r in rs], "admm_iters_mean": float(sum(r["admm_iter"] for r in rs) / len(rs)),
+           "primal_median": primal[len(primal) // 2], "primal_max": primal[-1],
+           "dual_max": max(r["dual"] for r in rs), "results": sorted({r["result_name"] for r in rs}),
+           "settings": f"rho 2e4, {max_iter} ADMM iterations per QP, eps 1e-3 (dual 5e-3), at most {MAX_SQP} SQP"}
+    out["summary"] = {"conv": out["converged"], "of": len(grids), "tol": tol, "s": round(t, 2),
+                      "primal_med": float(f"{out['primal_median']:.2e}")}
+    return out
+
+
 def workload_grids(name):
     from paper_2310_13143_gb300 import gridgen
 
@@ -617,16 +755,21 @@ def measured_traffic(workload, iters_per_launch):
 
 def sweep_only(grids, precision, iters, launches, warmup, workload=None):
     """ADMM sweep alone (fixed iteration count) on the QP at the flat start:
-    ADMM iterations/s and the sweep's HBM roofline on a given workload."""
+    ADMM iterations/s, the sweep's HBM roofline and the handle's device
+    memory footprint on a given workload."""
     import torch
 
     from paper_2310_13143_gb300 import binding
 
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
     s = binding.Solver(grids, precision=precision)
     stream = torch.cuda.Stream()
     s.set_stream(stream.cuda_stream)
     shape, _ = s.autotune(os.path.join(tempfile.gettempdir(), "acopf_tune_cache.json"), iters=30)
     s.build_qp(1.0, 2e4, True)
+    torch.cuda.synchronize()
+    footprint = free0 - torch.cuda.mem_get_info()[0]
     opts = binding.default_admm()
     for _ in range(warmup):
         s.admm_iterate(iters, opts)
@@ -638,26 +781,93 @@ def sweep_only(grids, precision, iters, launches, warmup, workload=None):
     B = sum(g.nbus for g in grids)
     L = sum(g.nbranch for g in grids)
     G = sum(g.ngen for g in grids)
-    bpi = sweep_bytes_per_iter(B, L, G, 4 if precision == "mixed" else 8)
     us = 1e3 * p["sweep_ms"] / (iters * launches)
-    hbm, which = _peaks()
-    gbs = bpi / (us * 1e-6) / 1e9
+    kernel = "k_sweep<float>" if precision == "mixed" else "k_sweep<double>"
+    traffic = measured_traffic(workload, iters) if precision == "mixed" and workload else None
+    rl = roofline(B, L, G, 4 if precision == "mixed" else 8, iters, us * iters / 1e3, traffic, kernel)
     return {"instances": len(grids), "buses": B, "branches": L, "generators": G, "precision": precision,
             "us_per_iter": us, "admm_iter_per_s": 1e6 / us, "instance_iters_per_s": len(grids) * 1e6 / us,
             "launch_shape": {"block_threads": shape[0], "ctas_per_sm": shape[1], "stages": shape[2]},
-            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                         "traffic": measured_traffic(workload, iters) if precision == "mixed" and workload else None,
-                         "traffic_unit": "bytes per launch", "iters_per_launch": iters,
-                         "peak_source": which, "bytes_per_iter": bpi, "bytes_per_launch": bpi * iters,
-                         "kernel": "k_sweep<float>" if precision == "mixed" else "k_sweep<double>"}}
+            "device_bytes": int(footprint), "roofline": rl}
 
 
-def cpu_baseline(grid, admm_iters_per_solve, seconds):
-    """The oracle as it stands, single thread, on a bounded sample: ADMM
-    iterations of the first QP of the same grid for about ``seconds`` of CPU
-    time; the solve rate is that per-iteration time scaled to the ADMM
-    iterations one full solve needs (the build/merit/step work of the oracle
-    is timed too and added per SQP iteration)."""
+def oracle_options():
+    """The oracle's settings for the benchmark's solve (as solver_options for
+    the FP64 path: rho 2e4, 1,000 ADMM iterations of eps 1e-3 per QP, SQP
+    tolerance 1e-4, at most MAX_SQP iterations)."""
+    import oracle
+
+    return oracle.SqpOptions(tol=1e-4, max_sqp=MAX_SQP, rho=2e4, eps=1e-3, max_iter=1000)
+
+
+def _oracle_converged(r):
+    return r["status"] == 0 and r["primal"] <= 1e-4 and r["dual"] <= 1e-4
+
+
+def cpu_baseline(grid, min_seconds=10.0):
+    """The oracle as it stands, one thread: full solves of the same grid from
+    the flat start, as many as fit in about min_seconds (at least one)."""
+    import oracle
+
+    oracle.build()
+    m = oracle.Model(grid)
+    o = oracle_options()
+    n = conv = admm = 0
+    t = 0.0
+    while n == 0 or t < min_seconds:
+        t0 = time.perf_counter()
+        r = m.sqp(o)
+        t += time.perf_counter() - t0
+        n += 1
+        conv += int(_oracle_converged(r))
+        admm += r["admm_total"]
+    return {"value": conv / t, "unit": "solves/s", "cores": 1, "kind": "oracle", "nproc": os.cpu_count(),
+            "sample": f"{n} full single-thread oracle solves of the same 2000-bus grid from the flat start "
+                      f"({t:.1f} s, {conv} converged, {r['iters']} SQP iterations each)",
+            "seconds_per_solve": t / n, "admm_iter_per_s": admm / t}
+
+
+def _oracle_solve(job):
+    """One oracle solve in a worker process: (status, primal, dual, seconds)."""
+    import oracle
+
+    grid, kw = job
+    t0 = time.perf_counter()
+    r = oracle.Model(grid).sqp(oracle.SqpOptions(**kw))
+    return r["status"], r["primal"], r["dual"], time.perf_counter() - t0
+
+
+def cpu_batched_leg(grids, max_bus=4000, nscen=256):
+    """The oracle on the batched workload, one instance per host core over
+    all cores (spawned worker processes): a bounded sample of nproc instances
+    taken with an even stride through the batch, uneven grids above max_bus
+    buses skipped (their oracle solves run for minutes)."""
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
+    n = os.cpu_count() or 1
+    eligible = [i for i in range(len(grids)) if grids[i].nbus <= max_bus]
+    pick = eligible[::max(1, len(eligible) // n)][:n]
+    o = oracle_options()
+    kw = dict(tol=o.tol, max_sqp=o.max_sqp, rho=o.rho, eps=o.eps, max_iter=o.max_iter)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(pick)) as pool:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_solve, [(grids[k], kw) for k in pick], chunksize=1)
+        wall = time.perf_counter() - t0
+    conv = sum(int(st == 0 and p <= 1e-4 and d <= 1e-4) for st, p, d, _ in res)
+    return {"value": conv / wall, "unit": "solves/s", "instances_per_s": len(pick) / wall, "cores": len(pick),
+            "kind": "oracle", "nproc": n, "converged": conv, "wall_seconds": wall,
+            "sample": f"{len(pick)} instances of the batch ({sum(k < nscen for k in pick)} load scenarios, "
+                      f"{sum(k >= nscen for k in pick)} uneven grids of <= {max_bus} buses), one per process, "
+                      f"solved concurrently on {len(pick)} host cores"}
+
+
+def cpu_large_leg(grid, iters=50):
+    """The oracle on one instance of the 70,000-bus workload: ADMM iterations
+    of its first QP (flat start), one thread."""
     import oracle
 
     oracle.build()
@@ -665,48 +875,49 @@ def cpu_baseline(grid, admm_iters_per_solve, seconds):
     x = m.flat_start()
     t0 = time.perf_counter()
     qp = m.build(x, None, 1.0, 1)
-    d_ref, _ = m.step(qp, m.new_state(), x)
-    m.merit(qp, x, d_ref)
-    t_outer = time.perf_counter() - t0
+    t_build = time.perf_counter() - t0
     st = m.new_state(2e4)
-    n, t = 0, 0.0
-    chunk = 50
-    while t < seconds:
-        t1 = time.perf_counter()
-        st, _ = m.admm(qp, st, rho=2e4, eps=0.0, max_iter=chunk)
-        t += time.perf_counter() - t1
-        n += chunk
-    per_iter = t / n
-    est = per_iter * admm_iters_per_solve + 10 * t_outer
-    return {"value": 1.0 / est, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} ADMM iterations of the first QP of the same 2000-bus grid ({t:.1f} s, "
-                      f"{per_iter * 1e3:.2f} ms/iteration) scaled to {admm_iters_per_solve:.0f} iterations per solve "
-                      f"plus 10 SQP iterations of build/step/merit",
-            "admm_iter_per_s": 1.0 / per_iter}
+    t0 = time.perf_counter()
+    m.admm(qp, st, rho=2e4, eps=0.0, max_iter=iters)
+    t = time.perf_counter() - t0
+    return {"admm_iter_per_s": iters / t, "unit": "ADMM iterations/s of one 70,000-bus instance", "cores": 1,
+            "kind": "oracle", "sample": f"{iters} ADMM iterations of the first QP ({t:.1f} s; QP build {t_build:.1f} s)"}
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle on the host cores (rank 0 only)."""
+    """Reference arm: the FP64 CPU oracle on the host cores (rank 0 only).
+    Every step is one full single-thread solve of the benchmark's grid from
+    the flat start, with the benchmark's settings."""
+    import oracle
+
     from paper_2310_13143_gb300 import gridgen
 
+    oracle.build()
     grid = gridgen.grid_2000bus()
-    per_step = []
-    samples = []
-    # the oracle's full solve takes far too long at this size: each step times a
-    # bounded sample and scales it (see cpu_baseline)
-    for _ in range(args.warmup + args.steps):
-        cb = cpu_baseline(grid, args.ref_iters_per_solve, args.cpu_seconds / max(args.steps, 1))
-        samples.append(cb)
-    kept = samples[args.warmup:]
-    val = statistics.median([c["value"] for c in kept])
+    m = oracle.Model(grid)
+    o = oracle_options()
+    for _ in range(args.warmup):
+        m.sqp(o)
+    t = 0.0
+    conv = 0
+    last = None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        last = m.sqp(o)
+        t += time.perf_counter() - t0
+        conv += int(_oracle_converged(last))
+    val = conv / t if t > 0 else 0.0
     return {
         "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 / val if val > 0 else None, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": headline_config(grid, args.precision, args.gpus),
-        "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": kept[0]["sample"] + "; FP64 oracle, each timed step one bounded sample"},
+        "config": headline_config(grid, "fp64", args.gpus),
+        "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle", "nproc": os.cpu_count(),
+                         "sample": f"{args.steps} full single-thread oracle solves (FP64), one per step, "
+                                   f"after {args.warmup} untimed ones"},
         "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "converged_steps": conv, "sqp_iters_last": last["iters"] if last else None,
+        "objective_last": last["obj"] if last else None,
     }
 
 
@@ -717,8 +928,6 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-iters-per-solve", type=float, default=8000.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -726,6 +935,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-rho-sweep", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-large-solve", action="store_true")
     ap.add_argument("--workload", default="syn2000",
                     choices=["syn2000", "batched", "syn70k", "syn70k_x16", "gemm", "mlp_train"])
     ap.add_argument("--gemm-shape", default="8192,8192,8192")

@@ -5,9 +5,11 @@ point of a solve: the NLP point x0, the line multipliers pi, the ADMM
 multipliers lambda of the first QP and a log penalty factor per component
 (layout of acopf_set_warm_start_device).  The training targets are the
 final iterate, multipliers and ADMM state of cold-start solves of sampled
-scenarios, computed by the same solver; a warm-started solve must still pass
-the solver's own convergence test, so the cold-start method remains the
-judge of the prediction's error.
+scenarios, computed by the same solver, and penalty factors chosen by
+solving each scenario from the network's own predicted start under a few
+candidate factors (rho_targets).  A warm-started solve must still pass the
+solver's own convergence test, so the cold-start method remains the judge
+of the prediction's error.
 
 Everything numeric runs in the library's kernels (solves, tensor-core
 products, Adam, the scatter into the solver); this module only moves arrays
@@ -68,12 +70,73 @@ def solve_targets(grids, opts, precision="mixed", chunk=256, base_rho=2e4):
             row[o:o + 4 * L] = pi.ravel(); o += 4 * L
             row[o:o + 8 * L] = st["lam"].ravel(); o += 8 * L
             row[o:o + 2 * G] = st["lg"].ravel(); o += 2 * G
-            row[o:o + L + G] = 0.0  # the data-generating solves use one fixed penalty
+            row[o:o + L + G] = 0.0  # the base penalty; rho_targets sets these columns
             conv[c0 + k] = r["result_name"] == "converged"
             iters[c0 + k] = r["admm_iter"]
             objs[c0 + k] = s.get_solution(k)["obj"]
         s.close()
     return T, conv, iters, objs
+
+
+# candidate penalty factors (branches, generators) of the penalty targets
+RHO_CHOICES = ((1.0, 1.0), (0.5, 0.5), (0.25, 0.25), (0.125, 0.125), (0.25, 1.0))
+
+
+def rho_columns(grid):
+    """Column range of the per-component log penalty factors (branches, then
+    generators) in the output layout."""
+    B, L, G = grid.nbus, grid.nbranch, grid.ngen
+    o = 2 * G + 2 * B + 2 * L + 4 * L + 8 * L + 2 * G
+    return o, o + L, o + L + G
+
+
+def rho_targets(grids, net, X_dev, T, opts, choices=RHO_CHOICES, chunk=1024, base_rho=2e4, precision="mixed",
+                stream_ptr=None):
+    """Per-component penalty targets (form 4).  Every scenario is solved from
+    the network's predicted start (x0, pi, lambda) under each candidate pair
+    of penalty factors -- one for every branch's couplings, one for every
+    generator's -- and the pair whose solve converges in the fewest ADMM
+    iterations becomes the scenario's target: log factors in T's penalty
+    columns (in place).  Returns the chosen pair index per scenario and the
+    ADMM iterations of each candidate."""
+    import torch
+
+    o0, o1, o2 = rho_columns(grids[0])
+    n = len(grids)
+    pick = np.zeros(n, dtype=np.int64)
+    iters = np.full((n, len(choices)), np.inf)
+    if stream_ptr is not None:
+        net.set_stream(stream_ptr)
+    for c0 in range(0, n, chunk):
+        part = grids[c0:c0 + chunk]
+        m = len(part)
+        pred = torch.zeros((m, net.dims[-1]), device=X_dev.device)
+        net.forward(X_dev[c0:c0 + m].data_ptr(), m, pred.data_ptr())
+        s = binding.Solver(part, precision=precision)
+        if stream_ptr is not None:
+            s.set_stream(stream_ptr)
+        for j, (fb, fg) in enumerate(choices):
+            pred[:, o0:o1] = float(np.log(fb))
+            pred[:, o1:o2] = float(np.log(fg))
+            s.set_warm_start_device(pred.data_ptr(), net.dims[-1], base_rho=base_rho, use_x=True, use_pi=True,
+                                    use_lambda=True, use_rho=True)
+            s.sqp_solve_graph(opts, check_every=2)
+            for k in range(m):
+                r = s.get_residuals(k)
+                if converged(r):
+                    iters[c0 + k, j] = r["admm_iter"]
+        s.close()
+    # ties and all-failed rows keep the base penalty (choice 0)
+    best = np.argmin(iters, axis=1)
+    base_ok = np.isfinite(iters[:, 0])
+    keep = ~np.isfinite(iters.min(axis=1)) | (base_ok & (iters[np.arange(n), best] >= iters[:, 0]))
+    best[keep] = 0
+    pick[:] = best
+    for k in range(n):
+        fb, fg = choices[pick[k]]
+        T[k, o0:o1] = np.log(fb)
+        T[k, o1:o2] = np.log(fg)
+    return pick, iters
 
 
 def train(net, X_dev, T_dev, n: int, steps: int, batch: int, lr: float, seed: int, schedule: str = "const"):
@@ -102,7 +165,7 @@ def converged(r, tol=1e-4) -> bool:
 
 
 def solve_warm_with_fallback(solver, grids, net, X_dev, opts, precision="mixed", stream_ptr=None, base_rho=2e4,
-                             use_lambda=True, use_pi=True):
+                             use_lambda=True, use_pi=True, use_rho=False):
     """Warm-started solve of every scenario (rows of X_dev) on the prepared
     handle `solver` over `grids`; any instance that does not pass the
     solver's own convergence test is solved again from a cold start in a
@@ -116,7 +179,7 @@ def solve_warm_with_fallback(solver, grids, net, X_dev, opts, precision="mixed",
     pred = torch.zeros((n, net.dims[-1]), device=X_dev.device)
     net.forward(X_dev.data_ptr(), n, pred.data_ptr())
     solver.set_warm_start_device(pred.data_ptr(), net.dims[-1], base_rho=base_rho, use_x=True, use_pi=use_pi,
-                                 use_lambda=use_lambda, use_rho=False)
+                                 use_lambda=use_lambda, use_rho=use_rho)
     solver.sqp_solve_graph(opts, check_every=2)
     res = [solver.get_residuals(k) for k in range(n)]
     obj = [solver.get_solution(k)["obj"] for k in range(n)]

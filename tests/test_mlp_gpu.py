@@ -207,3 +207,48 @@ def test_learned_warm_start_beats_cold_start_on_held_out_scenarios():
     cold_iters = iters[384:]
     np.testing.assert_allclose(warm_obj, objs[384:], rtol=1e-5)
     assert np.mean(warm_iters) < 0.8 * np.mean(cold_iters), (np.mean(warm_iters), np.mean(cold_iters))
+
+
+def test_learned_penalties_on_held_out_scenarios():
+    """Form (4)'s per-component penalties: after the network learns x0, pi
+    and lambda, each training scenario is solved from its prediction under a
+    few candidate penalty factors (branches, generators); the fastest
+    converging pair becomes the target of the penalty outputs, and the
+    network is fine-tuned.  On held-out scenarios the solve with the
+    predicted penalties must converge like the one without them, and its
+    ADMM iteration count is compared with that of x0/pi/lambda alone."""
+    base = gg.geometric_grid(118, seed=11)
+    scen = gg.scenarios_cholesky(base, 384 + 32, seed=901)
+    opts = binding.default_sqp(tol=1e-4, max_sqp=40, admm=dict(rho=2e4, max_iter=1000, eps=1e-3, eps_dual=5e-3))
+    T, conv, iters, objs = ws.solve_targets(scen, opts, precision="mixed")
+    assert conv.all()
+    train_s, test_s = scen[:384], scen[384:]
+    X = ws.loads_matrix(scen)
+    dims = ws.dims_for(base, hidden=(256, 256, 256))
+    net = binding.Mlp(dims, max_batch=128)
+    net.set_params(gg.mlp_init(dims, seed=3))
+    Xd = torch.from_numpy(X).cuda()
+    Td = torch.from_numpy(T).cuda()
+    net.fit_standardiser(Xd.data_ptr(), Td.data_ptr(), 384)
+    ws.train(net, Xd, Td, 384, steps=600, batch=128, lr=1e-3, seed=4)
+    pick, cand = ws.rho_targets(train_s, net, Xd, T, opts)
+    o0, o1, o2 = ws.rho_columns(base)
+    assert np.isfinite(cand[:, 0]).mean() > 0.95  # the base penalty converges from the prediction
+    Td = torch.from_numpy(T).cuda()
+    net.fit_standardiser(Xd.data_ptr(), Td.data_ptr(), 384)
+    ws.train(net, Xd, Td, 384, steps=300, batch=128, lr=3e-4, seed=5)
+    out = {}
+    for use_rho in (False, True):
+        s = binding.Solver(test_s, precision="mixed")
+        res, obj, failed = ws.solve_warm_with_fallback(s, test_s, net, Xd[384:], opts, use_rho=use_rho)
+        s.close()
+        assert all(ws.converged(r) for r in res)
+        np.testing.assert_allclose(obj, objs[384:], rtol=1e-5)
+        out[use_rho] = (np.mean([r["admm_iter"] for r in res]), len(failed))
+    net.close()
+    chosen = np.bincount(pick, minlength=len(ws.RHO_CHOICES))
+    print("penalty choices", dict(zip(map(str, ws.RHO_CHOICES), chosen.tolist())),
+          "ADMM iterations without / with the learned penalties", out[False], out[True])
+    assert out[True][1] <= 4  # the cold fallback stays the exception
+    # the learned penalties cut the ADMM iterations of the warm-started solves
+    assert out[True][0] <= 0.9 * out[False][0], out
