@@ -78,8 +78,12 @@ def solve_targets(grids, opts, precision="mixed", chunk=256, base_rho=2e4):
     return T, conv, iters, objs
 
 
-# candidate penalty factors (branches, generators) of the penalty targets
-RHO_CHOICES = ((1.0, 1.0), (0.5, 0.5), (0.25, 0.25), (0.125, 0.125), (0.25, 1.0))
+# candidate penalty factors (branches, generators) of the penalty targets.
+# Factors below 0.5 win narrowly on many training scenarios but sit at the
+# edge of stability: on held-out scenarios of the 2,000-bus grid a constant
+# 0.35 left 21 of 512 warm-started solves unconverged and 0.25 left 124,
+# while 0.5 converged all of them with 0.72x the ADMM iterations of 1.
+RHO_CHOICES = ((1.0, 1.0), (0.75, 0.75), (0.5, 0.5), (0.5, 1.0), (0.5, 0.75))
 
 
 def rho_columns(grid):
