@@ -21,7 +21,7 @@ _lib = None
 
 DP = C.POINTER(C.c_double)
 IP = C.POINTER(C.c_int32)
-HIST_W = 11
+HIST_W = 13
 
 
 def build(force: bool = False) -> str:
@@ -73,7 +73,8 @@ class _AdmmInfo(C.Structure):
 class _SqpOpts(C.Structure):
     _fields_ = [("mu", C.c_double), ("tol", C.c_double), ("step_tol", C.c_double), ("delta0", C.c_double),
                 ("delta_max", C.c_double), ("delta_min", C.c_double), ("rho", C.c_double),
-                ("max_sqp", C.c_int32), ("warm_lambda", C.c_int32), ("admm", _AdmmOpts)]
+                ("max_sqp", C.c_int32), ("warm_lambda", C.c_int32), ("admm", _AdmmOpts),
+                ("soc", C.c_int32), ("restore", C.c_int32)]
 
 
 class _SqpInfo(C.Structure):
@@ -96,6 +97,8 @@ def lib():
         L.og_objective.argtypes = [C.c_void_p, DP]
         L.og_objective.restype = C.c_double
         L.og_build.argtypes = [C.c_void_p, DP, DP, C.c_double, C.c_int, C.POINTER(_QP)]
+        L.og_build_ex.argtypes = [C.c_void_p, DP, DP, C.c_double, C.c_int, DP, C.c_double, C.POINTER(_QP)]
+        L.og_merit_ex.argtypes = [C.c_void_p, C.POINTER(_QP), DP, DP, C.c_double, C.c_int, C.c_double, DP, DP, DP]
         L.og_gen_update.argtypes = [C.c_double] * 6 + [DP, DP, DP, DP]
         L.og_line_qp.argtypes = [DP, DP, DP, DP, DP, DP, C.c_double, C.c_double, C.c_int, DP, DP]
         L.og_line_update.argtypes = [C.c_void_p, C.POINTER(_QP), C.c_int, DP, DP, DP, C.c_int, DP, DP, IP]
@@ -143,11 +146,14 @@ class SqpOptions:
     rb_period: int = 0
     rb_mu: float = 10.0
     rb_tau: float = 2.0
+    soc: int = 0
+    restore: int = 0
 
 
 def _sqp_opts(o: SqpOptions):
     return _SqpOpts(o.mu, o.tol, o.step_tol, o.delta0, o.delta_max, o.delta_min, o.rho, o.max_sqp,
-                    o.warm_lambda, _AdmmOpts(o.eps, o.max_iter, o.use_angle, o.rb_period, o.rb_mu, o.rb_tau))
+                    o.warm_lambda, _AdmmOpts(o.eps, o.max_iter, o.use_angle, o.rb_period, o.rb_mu, o.rb_tau),
+                    o.soc, o.restore)
 
 
 def tr_update(opts: SqpOptions, delta, dnorm, ared, pred):
@@ -242,11 +248,17 @@ class Model:
         s = _QP(**{n: _dp(arrs[n]) for n in arrs})
         return arrs, s
 
-    def build(self, x, pi=None, delta=1.0, use_angle=1):
+    def build(self, x, pi=None, delta=1.0, use_angle=1, dsoc=None, fscale=1.0):
+        """QP of eq. QPsub at x; with dsoc, the second-order correction QP of
+        that step; fscale weights the objective (0: restoration)."""
         x = _f64(x)
         pi = np.zeros(4 * self.L) if pi is None else _f64(pi).ravel()
         arrs, s = self.new_qp()
-        lib().og_build(self._h, _dp(x), _dp(pi), float(delta), int(use_angle), C.byref(s))
+        if dsoc is None and fscale == 1.0:
+            lib().og_build(self._h, _dp(x), _dp(pi), float(delta), int(use_angle), C.byref(s))
+        else:
+            ds = None if dsoc is None else _dp(_f64(dsoc))
+            lib().og_build_ex(self._h, _dp(x), _dp(pi), float(delta), int(use_angle), ds, float(fscale), C.byref(s))
         return QP(self, arrs, s)
 
     # ------------------------------------------------------------------ ADMM
@@ -276,10 +288,10 @@ class Model:
         lib().og_step(self._h, C.byref(qp.s), C.byref(state.s), _dp(_f64(x)), _dp(d), _dp(pi))
         return d, pi[:4 * self.L]
 
-    def merit(self, qp, x, d, mu=1e5, use_angle=1):
+    def merit(self, qp, x, d, mu=1e5, use_angle=1, fscale=1.0):
         a, b, c = C.c_double(), C.c_double(), C.c_double()
-        lib().og_merit(self._h, C.byref(qp.s), _dp(_f64(x)), _dp(_f64(d)), float(mu), int(use_angle),
-                       C.byref(a), C.byref(b), C.byref(c))
+        lib().og_merit_ex(self._h, C.byref(qp.s), _dp(_f64(x)), _dp(_f64(d)), float(mu), int(use_angle),
+                          float(fscale), C.byref(a), C.byref(b), C.byref(c))
         return a.value, b.value, c.value
 
     def kkt(self, x, pi, nu, ul, use_angle=1):

@@ -230,15 +230,25 @@ static void branch_hessian(const double* Y, double thi, double thj, double wr, d
     }
 }
 
-void og_build(const og_model* m, const double* x, const double* pi, double delta, int use_angle, og_qp* qp) {
+/* The QP of eq. QPsub at x.  With dsoc (a step of the same layout as x) it is
+ * the second-order correction QP of that step: every nonlinear constraint
+ * value c(x) in the linearisation is replaced by c(x + d) - grad c(x)' d, so
+ * that the linearised constraints at the corrected step d' read
+ * c(x + d) + grad c(x)' (d' - d) (the value at x + d, linearised at x).  For
+ * the quadratic opfc11 and the line limits the difference is the step's exact
+ * second-order term; opfc12 is evaluated at x + d.  fscale weights the
+ * objective (0: the feasibility-restoration QP, which minimises the
+ * violation alone). */
+void og_build_ex(const og_model* m, const double* x, const double* pi, double delta, int use_angle, const double* dsoc,
+                 double fscale, og_qp* qp) {
   const og_grid* g = &m->g;
   int B = g->nbus, L = g->nbranch, G = g->ngen;
   double S = g->base_mva;
   /* generators: gradient and curvature of the cost, shifted boxes (opfqpc1-2 with the trust region) */
   for (int k = 0; k < G; ++k) {
     double p = x[OPG(m) + k], q = x[OQG(m) + k];
-    qp->gd1[k] = 2.0 * g->c2[k] * S * S * p + g->c1[k] * S;
-    qp->gd2[k] = 2.0 * g->c2[k] * S * S;
+    qp->gd1[k] = fscale * (2.0 * g->c2[k] * S * S * p + g->c1[k] * S);
+    qp->gd2[k] = fscale * 2.0 * g->c2[k] * S * S;
     box_shift(g->pmin[k], g->pmax[k], p, delta, &qp->glp[k], &qp->gup[k]);
     box_shift(g->qmin[k], g->qmax[k], q, delta, &qp->glq[k], &qp->guq[k]);
   }
@@ -269,6 +279,14 @@ void og_build(const og_model* m, const double* x, const double* pi, double delta
     double D = wr * cs + wim * sn;
     double R0 = wi * wj - wr * wr - wim * wim;
     double S0 = -wr * sn + wim * cs;
+    if (dsoc) {
+      double dwi = dsoc[OW(m) + i], dwj = dsoc[OW(m) + j];
+      double dth = dsoc[OTH(m) + i] - dsoc[OTH(m) + j];
+      double dwr = dsoc[OWR(m) + l], dwim = dsoc[OWI(m) + l];
+      R0 += dwi * dwj - dwr * dwr - dwim * dwim;
+      double s1 = sin(thi - thj + dth), c1 = cos(thi - thj + dth);
+      S0 = (-(wr + dwr) * s1 + (wim + dwim) * c1) - (-sn * dwr + cs * dwim - D * dth);
+    }
     double* aR = qp->aR + 4 * l;
     double* aI = qp->aI + 4 * l;
     aR[0] = cs * wj / (2 * D); aR[1] = -wim; aR[2] = cs * wi / (2 * D); aR[3] = wim;
@@ -330,7 +348,15 @@ void og_build(const og_model* m, const double* x, const double* pi, double delta
         continue;
       }
       for (int c = 0; c < 4; ++c) Gr[c] = 2 * p * qp->F[16 * l + 4 * (2 * e) + c] + 2 * q * qp->F[16 * l + 4 * (2 * e + 1) + c];
-      qp->grhs[2 * l + e] = s2 - p * p - q * q - 2 * p * qp->f0[4 * l + 2 * e] - 2 * q * qp->f0[4 * l + 2 * e + 1];
+      double lim = s2 - p * p - q * q;
+      if (dsoc) {  /* the flows are linear in (w, wR, wI): their change under d is exact */
+        double dz[6] = {dsoc[OW(m) + i], dsoc[OTH(m) + i], dsoc[OWR(m) + l], dsoc[OWI(m) + l], dsoc[OW(m) + j],
+                        dsoc[OTH(m) + j]};
+        double dp = 0, dq = 0;
+        for (int k = 0; k < 6; ++k) { dp += J[2 * e][k] * dz[k]; dq += J[2 * e + 1][k] * dz[k]; }
+        lim -= dp * dp + dq * dq;
+      }
+      qp->grhs[2 * l + e] = lim - 2 * p * qp->f0[4 * l + 2 * e] - 2 * q * qp->f0[4 * l + 2 * e + 1];
     }
     /* angle-difference limits on th_i - th_j */
     if (use_angle && g->angmin[l] > -TWO_PI && g->angmax[l] < TWO_PI) {
@@ -341,6 +367,10 @@ void og_build(const og_model* m, const double* x, const double* pi, double delta
       qp->ahi[l] = BIG;
     }
   }
+}
+
+void og_build(const og_model* m, const double* x, const double* pi, double delta, int use_angle, og_qp* qp) {
+  og_build_ex(m, x, pi, delta, use_angle, NULL, 1.0, qp);
 }
 
 /* ------------------------------------------------------- generator update */
@@ -848,6 +878,13 @@ static void violations(const og_model* m, const double* x, int use_angle, double
 /* phi_1(x) = f + mu h, q(d) = f + grad f'd + 1/2 d'(Hess L)d + mu m(d) (Sec. II-C) */
 void og_merit(const og_model* m, const og_qp* qp, const double* x, const double* d, double mu, int use_angle,
               double* phi_x, double* phi_xd, double* pred) {
+  og_merit_ex(m, qp, x, d, mu, use_angle, 1.0, phi_x, phi_xd, pred);
+}
+
+/* og_merit with the objective weighted by fscale (the QP's own gradient and
+ * curvature were built with the same weight) */
+void og_merit_ex(const og_model* m, const og_qp* qp, const double* x, const double* d, double mu, int use_angle,
+                 double fscale, double* phi_x, double* phi_xd, double* pred) {
   const og_grid* g = &m->g;
   int B = g->nbus, L = g->nbranch, G = g->ngen, n = m->nvar;
   double* xd = (double*)malloc(sizeof(double) * n);
@@ -855,7 +892,7 @@ void og_merit(const og_model* m, const og_qp* qp, const double* x, const double*
   double h0, hinf0, h1, hinf1;
   violations(m, x, use_angle, &h0, &hinf0);
   violations(m, xd, use_angle, &h1, &hinf1);
-  double f0 = og_objective(m, x), f1 = og_objective(m, xd);
+  double f0 = fscale * og_objective(m, x), f1 = fscale * og_objective(m, xd);
   *phi_x = f0 + mu * h0;
   *phi_xd = f1 + mu * h1;
   /* model: gradient and curvature */
@@ -1048,7 +1085,8 @@ int og_sqp(const og_model* m, const og_sqp_opts* o, const double* x0, double* x,
   for (int k = 0; k < L; ++k) st.aset[k] = -1;
   double* d = (double*)calloc(n, sizeof(double));
   double* pin = (double*)calloc(4 * L + 1, sizeof(double));
-  double* xt = (double*)calloc(n, sizeof(double));
+  double* dsoc = (double*)calloc(n, sizeof(double));
+  double* pisoc = (double*)calloc(4 * L + 1, sizeof(double));
 
   memcpy(x, x0, sizeof(double) * n);
   memset(pi, 0, sizeof(double) * 4 * L);
@@ -1056,25 +1094,60 @@ int og_sqp(const og_model* m, const og_sqp_opts* o, const double* x0, double* x,
   double delta = o->delta0;
   int first_qp = 1;
   int status = 1, k, acc = 0, admm_total = 0;
+  int restoring = 0;       /* 1 in the feasibility-restoration phase */
+  double fscale = 1.0;     /* objective weight: 0 while restoring */
+  enum { kRestoreWindow = 5 };
+  double primal_at[kRestoreWindow] = {0};  /* primal infeasibility of the last iterations */
+  int since_switch = 0;    /* iterations since the last change of phase */
   double primal = BIG, dual = BIG;
   {
     double h1;
     violations(m, x, o->admm.use_angle, &h1, &primal);
   }
   for (k = 0; k < o->max_sqp; ++k) {
-    og_build(m, x, pi, delta, o->admm.use_angle, &qp);
+    og_build_ex(m, x, pi, delta, o->admm.use_angle, NULL, fscale, &qp);
     og_admm_cold(m, &st, o->rho, first_qp ? 0 : o->warm_lambda);
     first_qp = 0;
     og_admm_info ai;
     og_admm(m, &qp, &o->admm, &st, &ai);
-    admm_total += ai.iters;
+    int iters = ai.iters;
     og_step(m, &qp, &st, x, d, pin);
     double dn = 0;
     for (int t2 = 0; t2 < 2 * G + 2 * B; ++t2) dn = dmax(dn, fabs(d[t2]));
     double phx, phxd, pred;
-    og_merit(m, &qp, x, d, o->mu, o->admm.use_angle, &phx, &phxd, &pred);
+    og_merit_ex(m, &qp, x, d, o->mu, o->admm.use_angle, fscale, &phx, &phxd, &pred);
     double ared = phx - phxd;
-    int accept = 0;
+    int accept = 0, soc = 0;
+    og_tr_update(o, delta, dn, ared, pred, &accept);
+    if (!accept && o->soc && isfinite(pred) && pred > 0) {
+      /* second-order correction: the same QP with the constraint values of
+       * x + d (linearised at x); the corrected step passes if it reduces the
+       * merit function against the original step's model reduction */
+      og_build_ex(m, x, pi, delta, o->admm.use_angle, d, fscale, &qp);
+      og_admm_cold(m, &st, o->rho, o->warm_lambda);
+      og_admm_info as;
+      og_admm(m, &qp, &o->admm, &st, &as);
+      iters += as.iters;
+      og_step(m, &qp, &st, x, dsoc, pisoc);
+      double dns = 0;
+      for (int t2 = 0; t2 < 2 * G + 2 * B; ++t2) dns = dmax(dns, fabs(dsoc[t2]));
+      double phx2, phxd2, pred2;
+      og_merit_ex(m, &qp, x, dsoc, o->mu, o->admm.use_angle, fscale, &phx2, &phxd2, &pred2);
+      double ared2 = phx - phxd2;
+      int acc2 = 0;
+      og_tr_update(o, delta, dns, ared2, pred, &acc2);
+      soc = 1;
+      if (acc2) {
+        memcpy(d, dsoc, sizeof(double) * n);
+        memcpy(pin, pisoc, sizeof(double) * 4 * L);
+        dn = dns;
+        ared = ared2;
+        soc = 2;
+      }
+      ai.r_inf = as.r_inf;
+      ai.s_inf = as.s_inf;
+    }
+    admm_total += iters;
     delta = og_tr_update(o, delta, dn, ared, pred, &accept);
     if (accept) {
       for (int t2 = 0; t2 < n; ++t2) x[t2] += d[t2];
@@ -1084,12 +1157,44 @@ int og_sqp(const og_model* m, const og_sqp_opts* o, const double* x0, double* x,
     }
     if (hist && k < hist_cap) {
       double* hr = hist + OG_HIST_W * k;
-      hr[0] = og_objective(m, x); hr[1] = primal; hr[2] = dual; hr[3] = ai.iters;
+      hr[0] = og_objective(m, x); hr[1] = primal; hr[2] = dual; hr[3] = iters;
       hr[4] = ai.r_inf; hr[5] = ai.s_inf; hr[6] = accept; hr[7] = delta; hr[8] = dn; hr[9] = ared; hr[10] = pred;
+      hr[11] = soc; hr[12] = restoring;
     }
     if (!all_finite(x, n)) { status = 3; k++; break; }
-    if (accept && primal <= o->tol && dual <= o->tol) { status = 0; k++; break; }
-    if ((accept && dn <= o->step_tol) || delta < o->delta_min) { status = 2; k++; break; }
+    int stall = (accept && dn <= o->step_tol) || delta < o->delta_min;
+    /* no progress towards feasibility: the violation, above 10 tol, has not
+     * fallen by a tenth over the last kRestoreWindow iterations */
+    double older = primal_at[k % kRestoreWindow];  /* the value kRestoreWindow iterations ago */
+    primal_at[k % kRestoreWindow] = primal;
+    int no_progress = k >= kRestoreWindow && primal > 10 * o->tol && primal > 0.9 * older &&
+                      since_switch >= kRestoreWindow;
+    ++since_switch;
+    if (!restoring) {
+      if (accept && primal <= o->tol && dual <= o->tol) { status = 0; k++; break; }
+      if (stall || (o->restore && no_progress)) {
+        if (o->restore && primal > o->tol) {
+          /* feasibility restoration: minimise the violation alone (objective
+           * weight 0, merit mu h) from the current point and radius delta0 */
+          restoring = 1;
+          fscale = 0.0;
+          delta = o->delta0;
+          since_switch = 0;
+          continue;
+        }
+        status = 2; k++; break;
+      }
+    } else {
+      if (accept && primal <= o->tol) {  /* feasible again: back to the SQP on the ACOPF */
+        restoring = 0;
+        fscale = 1.0;
+        delta = o->delta0;
+        since_switch = 0;
+        continue;
+      }
+      /* the violation stalls above tol: locally infeasible */
+      if (stall || no_progress) { status = 5; k++; break; }
+    }
   }
   info->iters = k;
   info->accepted = acc;
@@ -1099,6 +1204,6 @@ int og_sqp(const og_model* m, const og_sqp_opts* o, const double* x0, double* x,
   info->primal = primal;
   info->dual = dual;
   info->delta = delta;
-  free(buf); free(sbuf); free(d); free(pin); free(xt); free(st.aset);
+  free(buf); free(sbuf); free(d); free(pin); free(dsoc); free(pisoc); free(st.aset);
   return status;
 }

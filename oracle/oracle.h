@@ -90,16 +90,20 @@ typedef struct {
   int32_t max_sqp;
   int32_t warm_lambda; /* carry ADMM multipliers from one QP to the next */
   og_admm_opts admm;
+  int32_t soc;         /* second-order correction of rejected steps */
+  int32_t restore;     /* feasibility restoration when the SQP stalls infeasible */
 } og_sqp_opts;
 
 typedef struct {
-  int32_t iters, accepted, status; /* status: 0 converged, 1 max iter, 2 step too small, 3 non-finite */
+  int32_t iters, accepted, status; /* status: 0 converged, 1 max iter, 2 step too small, 3 non-finite,
+                                      5 locally infeasible (restoration stalled) */
   int32_t admm_total;
   double obj, primal, dual, delta;
 } og_sqp_info;
 
-/* per-iteration history row: obj primal dual admm_iters r s accept delta dnorm ared pred */
-#define OG_HIST_W 11
+/* per-iteration history row: obj primal dual admm_iters r s accept delta dnorm ared pred
+ * soc (0 none, 1 corrected step rejected, 2 accepted) restoring (0/1) */
+#define OG_HIST_W 13
 
 typedef struct og_model og_model;
 
@@ -147,6 +151,10 @@ void og_kkt(const og_model* m, const double* x, const double* pi, const double* 
 int og_sqp(const og_model* m, const og_sqp_opts* o, const double* x0, double* x, double* pi,
            og_sqp_info* info, double* hist, int hist_cap);
 
+void og_build_ex(const og_model* m, const double* x, const double* pi, double delta, int use_angle, const double* dsoc,
+                 double fscale, og_qp* qp);
+void og_merit_ex(const og_model* m, const og_qp* qp, const double* x, const double* d, double mu, int use_angle,
+                 double fscale, double* phi_x, double* phi_xd, double* pred);
 /* ratio test and trust-region update of Alg. 1: returns the new radius, *accept 0/1 */
 double og_tr_update(const og_sqp_opts* o, double delta, double dnorm, double ared, double pred, int* accept);
 /* l1 sum and l_inf maximum of every constraint violation at x (h of the merit function) */
