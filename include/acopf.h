@@ -51,7 +51,9 @@ typedef enum {
   ACOPF_MAXITER = 1,        /* SQP iteration limit reached */
   ACOPF_STEP_TOO_SMALL = 2, /* accepted step below step_tol, or trust region below delta_min */
   ACOPF_NONFINITE = 3,      /* a non-finite value appeared */
-  ACOPF_RUNNING = 4         /* no solve has finished for this instance */
+  ACOPF_RUNNING = 4,        /* no solve has finished for this instance */
+  ACOPF_INFEASIBLE = 5      /* locally infeasible: the feasibility restoration (sqp_options.restore)
+                               stalled with the primal infeasibility above tol */
 } acopf_result;
 
 enum { ACOPF_FP64 = 0, ACOPF_MIXED = 1 };
@@ -121,6 +123,17 @@ typedef struct {
                             inexact ADMM step does not satisfy exactly; 0: nonlinear constraints
                             only, as h is defined in Sec. II-C */
   admm_options admm;
+  int32_t soc;           /* 1: second-order correction of a rejected step (named as future work
+                            in Sec. II-D): the QP is rebuilt at x
+                            with every nonlinear constraint's value taken at x + d (linearised
+                            at x), solved, and x + d' passes the ratio test against the
+                            original step's model reduction; the history marks the outcome */
+  int32_t restore;       /* 1: feasibility restoration (likewise future work in the paper): when
+                            the SQP stalls (step or radius below its tolerance) or the primal
+                            infeasibility, above 10 tol, fails to fall by a tenth over five
+                            iterations, the objective is dropped (weight 0, merit mu h) until
+                            the infeasibility is within tol, then the SQP resumes from delta0;
+                            a stall during restoration ends with ACOPF_INFEASIBLE */
 } sqp_options;
 
 typedef struct {         /* caller-allocated host arrays (NULL to skip one) */
@@ -265,11 +278,13 @@ acopf_status acopf_get_solution(acopf_handle h, int32_t inst, acopf_solution* ou
  * instance or out. */
 acopf_status acopf_get_residuals(acopf_handle h, int32_t inst, acopf_residuals* out);
 
-/* Per-SQP-iteration history of the last sqp_solve for instance inst, 12 values
- * per iteration: objective, primal, dual, ADMM iterations, r, s, accepted (0/1),
- * trust radius after the update, step norm, actual and predicted merit
- * reduction, penalty factor of the last QP.  Writes at most cap rows, returns
- * the number of iterations in *n.  At most ACOPF_HIST_MAX rows are kept. */
+/* Per-SQP-iteration history of the last sqp_solve for instance inst, 14 values
+ * per iteration: objective, primal, dual, ADMM iterations (both passes), r, s,
+ * accepted (0/1), trust radius after the update, step norm, actual and
+ * predicted merit reduction, penalty factor of the last QP, second-order
+ * correction (0 none, 1 corrected step rejected, 2 accepted), restoration
+ * phase (0/1).  Writes at most cap rows, returns the number of iterations in
+ * *n.  At most ACOPF_HIST_MAX rows are kept. */
 #define ACOPF_HIST_MAX 64
 acopf_status acopf_get_history(acopf_handle h, int32_t inst, double* out, int32_t cap, int32_t* n);
 

@@ -19,7 +19,7 @@ FP = C.POINTER(C.c_float)
 IP = C.POINTER(C.c_int32)
 
 ACOPF_FP64, ACOPF_MIXED = 0, 1
-RESULTS = {0: "converged", 1: "max_iter", 2: "step_too_small", 3: "non_finite", 4: "running"}
+RESULTS = {0: "converged", 1: "max_iter", 2: "step_too_small", 3: "non_finite", 4: "running", 5: "infeasible"}
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTREADY"}
 
 
@@ -53,7 +53,7 @@ class admm_options(C.Structure):
 class sqp_options(C.Structure):
     _fields_ = [("mu", C.c_double), ("tol", C.c_double), ("step_tol", C.c_double), ("delta0", C.c_double),
                 ("delta_max", C.c_double), ("delta_min", C.c_double), ("max_sqp", C.c_int32),
-                ("merit_linear", C.c_int32), ("admm", admm_options)]
+                ("merit_linear", C.c_int32), ("admm", admm_options), ("soc", C.c_int32), ("restore", C.c_int32)]
 
 
 class acopf_solution(C.Structure):
@@ -407,14 +407,15 @@ class Solver:
         return d
 
     HIST_COLS = ("obj", "primal", "dual", "admm_iters", "r", "s", "accepted", "delta", "dnorm", "ared", "pred",
-                 "rho_factor")
+                 "rho_factor", "soc", "restoring")
 
     def get_history(self, inst=0):
-        out = np.zeros(64 * 12)
+        w = len(self.HIST_COLS)
+        out = np.zeros(64 * w)
         n = C.c_int32()
         self._check(lib().acopf_get_history(self.h, inst, _dp(out), 64, C.byref(n)))
         k = min(n.value, 64)
-        return out[:12 * k].reshape(k, 12)
+        return out[:w * k].reshape(k, w)
 
     def profile(self, on=True):
         self._check(lib().acopf_profile(self.h, int(bool(on))))

@@ -165,6 +165,8 @@ void sqp_default_options(sqp_options* o) {
   o->delta_min = 1e-8;
   o->max_sqp = 30;
   o->merit_linear = 1;
+  o->soc = 0;
+  o->restore = 0;
   admm_default_options(&o->admm);
 }
 
@@ -432,7 +434,7 @@ acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_o
   A(d.bar, 2); A(d.err, 1);
   A(d.flow_xd, 4 * (size_t)L); A(d.tbr, 8 * (size_t)L); A(d.tbus, 4 * (size_t)B); A(d.tgen, 8 * (size_t)G);
   A(d.dend, 2 * 2 * (size_t)L); A(d.red, 16 * (size_t)K); A(d.ctl, K); A(d.n_running, 1);
-  A(d.hist, (size_t)K * ACOPF_HIST_MAX * 12); A(d.rho_fac, K); A(d.phase_ns, 4);
+  A(d.hist, (size_t)K * ACOPF_HIST_MAX * kHistW); A(d.rho_fac, K); A(d.phase_ns, 4);
 #undef A
 #undef AR
   double *d_r = nullptr, *d_x = nullptr, *d_b = nullptr, *d_tap = nullptr, *d_sh = nullptr;
@@ -719,6 +721,10 @@ static acopf_status reset_control(Ctx* c, const sqp_options& o, bool fresh) {
     q.eps = o.admm.eps;
     q.result = ACOPF_RUNNING;
     q.merit_linear = o.merit_linear ? 1 : 0;
+    q.soc_on = o.soc ? 1 : 0;
+    q.restore_on = o.restore ? 1 : 0;
+    q.fscale = 1.0;
+    q.delta0 = o.delta0;
   }
   CK(cudaMemcpyAsync(d.ctl, ctl.data(), sizeof(InstCtl) * d.K, cudaMemcpyHostToDevice, c->stream));
   // copy back: the host vector is about to go out of scope
@@ -742,13 +748,30 @@ static acopf_status sweep_status(Ctx* c) {
   return ACOPF_OK;
 }
 
+// The correction pass of an SQP iteration (sqp_options.soc): for the instances
+// whose step the merit test rejected, the QP rebuilt with the constraint values
+// of x + d, solved by the same sweep, and its step judged against the original
+// model reduction; every other instance is skipped by each kernel.  Always
+// launched when soc is on, so that a captured iteration has a fixed shape.
+static acopf_status launch_soc_pass(Ctx& c, const sqp_options& o) {
+  if (!o.soc) return ACOPF_OK;
+  launch_build(c, false, 1);
+  launch_admm_reset(c, o.admm.warm, 1);
+  acopf_status s = launch_sweep(c, o.admm, 0);
+  if (s) return s;
+  launch_step(c, 1);
+  launch_merit(c, 1);
+  return ACOPF_OK;
+}
+
 acopf_status sqp_solve(acopf_handle h, const sqp_options* op) {
   Ctx* c = (Ctx*)h;
   if (!c) return ACOPF_EINVAL;
   sqp_options o;
   if (op) o = *op;
   else sqp_default_options(&o);
-  if (o.max_sqp < 1 || !(o.delta0 > 0) || !(o.mu >= 0)) return fail(c, ACOPF_EINVAL, "sqp options out of range");
+  if (o.max_sqp < 1 || !(o.delta0 > 0) || !(o.mu >= 0) || o.soc < 0 || o.soc > 1 || o.restore < 0 || o.restore > 1)
+    return fail(c, ACOPF_EINVAL, "sqp options out of range");
   acopf_status s = check_admm(o.admm, c);
   if (s) return s;
   if (!c->warm_x) launch_flat_start(*c);
@@ -764,6 +787,7 @@ acopf_status sqp_solve(acopf_handle h, const sqp_options* op) {
     if (o.admm.warm && o.admm.rb_period > 0) launch_commit_rho(*c);
     launch_step(*c);
     launch_merit(*c);
+    if ((s = launch_soc_pass(*c, o))) return s;
     launch_accept_and_kkt(*c);
     int running = 0;
     CK(cudaMemcpyAsync(&running, c->d.n_running, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -790,7 +814,8 @@ acopf_status sqp_solve_graph(acopf_handle h, const sqp_options* op, int32_t chec
   sqp_options o;
   if (op) o = *op;
   else sqp_default_options(&o);
-  if (o.max_sqp < 1 || !(o.delta0 > 0) || !(o.mu >= 0)) return fail(c, ACOPF_EINVAL, "sqp options out of range");
+  if (o.max_sqp < 1 || !(o.delta0 > 0) || !(o.mu >= 0) || o.soc < 0 || o.soc > 1 || o.restore < 0 || o.restore > 1)
+    return fail(c, ACOPF_EINVAL, "sqp options out of range");
   acopf_status s = check_admm(o.admm, c);
   if (s) return s;
   cudaStream_t user = c->stream;
@@ -815,6 +840,7 @@ acopf_status sqp_solve_graph(acopf_handle h, const sqp_options* op, int32_t chec
   if (o.admm.warm && o.admm.rb_period > 0) launch_commit_rho(*c);
   launch_step(*c);
   launch_merit(*c);
+  if ((s = launch_soc_pass(*c, o))) return s;
   launch_accept_and_kkt(*c);
   CK(cudaMemcpyAsync(c->h_running, c->d.n_running, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   if ((s = sweep_status(c))) return s;
@@ -831,6 +857,7 @@ acopf_status sqp_solve_graph(acopf_handle h, const sqp_options* op, int32_t chec
       if (o.admm.warm && o.admm.rb_period > 0) launch_commit_rho(*c);
       launch_step(*c);
       launch_merit(*c);
+      if (!cs) cs = launch_soc_pass(*c, o);
       launch_accept_and_kkt(*c);
       cudaMemcpyAsync(c->h_running, c->d.n_running, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
       cudaGraph_t g = nullptr;
@@ -1287,7 +1314,7 @@ acopf_status acopf_get_history(acopf_handle h, int32_t inst, double* out, int32_
   int rows = q.sqp_iter < ACOPF_HIST_MAX ? q.sqp_iter : ACOPF_HIST_MAX;
   int k = rows < cap ? rows : cap;
   if (k > 0)
-    CK(cudaMemcpy(out, c->d.hist + (size_t)inst * ACOPF_HIST_MAX * 12, sizeof(double) * 12 * k,
+    CK(cudaMemcpy(out, c->d.hist + (size_t)inst * ACOPF_HIST_MAX * kHistW, sizeof(double) * kHistW * k,
                   cudaMemcpyDeviceToHost));
   if (n) *n = q.sqp_iter;
   return ACOPF_OK;

@@ -34,6 +34,7 @@ constexpr double kBig = 1e30;
 //   52 alo  53 ahi  (angle-difference bounds on d_thi - d_thj; >= 1e29: none)
 //   54-55 2-norms of the two line-limit rows (0: row disabled)
 constexpr int kRecChunks = 14;
+constexpr int kHistW = 14;  // values per row of the SQP history (acopf_get_history)
 
 template <typename T>
 struct alignas(4 * sizeof(T)) V4 {
@@ -54,7 +55,24 @@ struct InstCtl {            // per-instance SQP control, device resident
   int32_t accept_last;
   int32_t admm_done;        // 1 once the ADMM residual test passed in the last sweep
   int32_t merit_linear;     // 1: h of the merit function includes the linear constraints
+  // second-order correction and feasibility restoration
+  int32_t soc_on, restore_on;  // options
+  int32_t soc_active;       // this iteration's step was rejected and is being corrected
+  int32_t soc_flag;         // last iteration: 0 no correction, 1 corrected step rejected, 2 accepted
+  int32_t restoring;        // 1 in the restoration phase (objective weight 0)
+  int32_t since_switch;     // iterations since the last change of phase
+  double fscale;            // objective weight of QP and merit function (1, or 0 while restoring)
+  double delta0;            // initial radius (restored at every change of phase)
+  double phx_saved, pred_saved, dn_saved, ared_saved;  // the rejected step's merit data
+  double primal_ring[5];    // primal infeasibility of the last five iterations
 };
+
+// instance k takes part in a pass of one SQP iteration: every running instance
+// in the main pass (0); in the correction pass (1) only those whose step was
+// rejected and is being corrected (second-order correction)
+__host__ __device__ inline bool live(const InstCtl& c, int pass) {
+  return c.result == ACOPF_RUNNING && (pass == 0 || c.soc_active);
+}
 
 // raw device pointers shared by all kernels
 struct Dev {
@@ -119,7 +137,7 @@ struct Dev {
   double* tgen;       // [8][G]
   double* dend;       // [2][2L] per-end gradient contributions (w, theta)
   double* red;        // [16][K] per-instance reductions
-  double* hist;       // [K][ACOPF_HIST_MAX][12] SQP history
+  double* hist;       // [K][ACOPF_HIST_MAX][kHistW] SQP history
   double* rho_fac;    // [K] penalty factor applied by residual balancing in the last sweep
   unsigned long long* phase_ns;  // [4] (profiling) CTA 0's time in phase A, first wait, phase B, second wait + test
   InstCtl* ctl;       // [K]
@@ -185,11 +203,11 @@ struct Ctx {
 // kernels, launchers (defined in the .cu files)
 void launch_setup(Ctx& c);
 void launch_flat_start(Ctx& c);
-void launch_build(Ctx& c, bool do_export);
-void launch_admm_reset(Ctx& c, int keep_lambda);
+void launch_build(Ctx& c, bool do_export, int pass = 0);
+void launch_admm_reset(Ctx& c, int keep_lambda, int pass = 0);
 acopf_status launch_sweep(Ctx& c, const admm_options& o, int fixed_iters);
-void launch_step(Ctx& c);
-void launch_merit(Ctx& c);
+void launch_step(Ctx& c, int pass = 0);
+void launch_merit(Ctx& c, int pass = 0);
 void launch_accept_and_kkt(Ctx& c);
 void launch_fill_rho(Ctx& c, double rho);
 void launch_commit_rho(Ctx& c);

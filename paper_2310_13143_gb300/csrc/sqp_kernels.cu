@@ -155,11 +155,11 @@ __global__ void k_flat_start(Dev d) {
 // subproblem's quadratic (with the ADMM penalty folded in), flow maps, boxes
 // and line-limit rows.  Optionally exports the FP64 QP data (110 per branch).
 template <typename T>
-__global__ void k_build_branch(Dev d, int use_angle, double* xbr) {
+__global__ void k_build_branch(Dev d, int use_angle, double* xbr, int pass) {
   int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= d.L) return;
   int k = d.br_inst[l];
-  if (d.ctl[k].result != ACOPF_RUNNING) return;
+  if (!live(d.ctl[k], pass)) return;
   double delta = d.ctl[k].delta;
   double rho = d.rho_l[l];
   Br b;
@@ -177,6 +177,18 @@ __global__ void k_build_branch(Dev d, int use_angle, double* xbr) {
   double D = b.wr * cs + b.wim * sn;
   double R0 = b.wi * b.wj - b.wr * b.wr - b.wim * b.wim;
   double S0 = -b.wr * sn + b.wim * cs;
+  // correction pass: the constraint values of x + d (d = the rejected step),
+  // linearised at x -- c(x + d) - grad c(x)' d; for the quadratic opfc11 that
+  // adds the step's second-order term, opfc12 is evaluated at x + d
+  double dz[6] = {0, 0, 0, 0, 0, 0};
+  if (pass) {
+    dz[0] = d.dw[b.i]; dz[1] = d.dth[b.i]; dz[2] = d.dwr[l]; dz[3] = d.dwi[l]; dz[4] = d.dw[b.j]; dz[5] = d.dth[b.j];
+    const double dth = dz[1] - dz[5];
+    R0 += dz[0] * dz[4] - dz[2] * dz[2] - dz[3] * dz[3];
+    double s1, c1;
+    sincos(b.thi - b.thj + dth, &s1, &c1);
+    S0 = (-(b.wr + dz[2]) * s1 + (b.wim + dz[3]) * c1) - (-sn * dz[2] + cs * dz[3] - D * dth);
+  }
   double aR[4] = {cs * b.wj / (2 * D), -b.wim, cs * b.wi / (2 * D), b.wim};
   double aI[4] = {sn * b.wj / (2 * D), b.wr, sn * b.wi / (2 * D), -b.wr};
   double bR = (cs * R0 + 2 * b.wim * S0) / (2 * D);
@@ -272,7 +284,16 @@ __global__ void k_build_branch(Dev d, int use_angle, double* xbr) {
       G[e][c] = 2 * p * F[2 * e][c] + 2 * q * F[2 * e + 1][c];
       nn += G[e][c] * G[e][c];
     }
-    grhs[e] = s2 - p * p - q * q - 2 * p * f0[2 * e] - 2 * q * f0[2 * e + 1];
+    double lim = s2 - p * p - q * q;
+    if (pass) {  // the flows are linear in (w, wR, wI): their change under d is exact
+      double dp = 0, dq = 0;
+      for (int c = 0; c < 6; ++c) {
+        dp += J[2 * e][c] * dz[c];
+        dq += J[2 * e + 1][c] * dz[c];
+      }
+      lim -= dp * dp + dq * dq;
+    }
+    grhs[e] = lim - 2 * p * f0[2 * e] - 2 * q * f0[2 * e + 1];
     gnorm[e] = sqrt(nn);
   }
   double alo = -kBig, ahi = kBig;
@@ -335,15 +356,16 @@ __global__ void k_build_branch(Dev d, int use_angle, double* xbr) {
 
 // generators: gradient/curvature of the cost, shifted boxes (opfqpc1-2 with the trust region)
 template <typename T>
-__global__ void k_build_gen(Dev d, double* xgen) {
+__global__ void k_build_gen(Dev d, double* xgen, int pass) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= d.G) return;
   int k = d.gen_inst[g];
-  if (d.ctl[k].result != ACOPF_RUNNING) return;
+  if (!live(d.ctl[k], pass)) return;
   double delta = d.ctl[k].delta;
+  const double fs = d.ctl[k].fscale;  // objective weight (0 while restoring feasibility)
   double p = d.pg[g], q = d.qg[g];
-  double g1 = 2.0 * d.cq[g] * p + d.cl[g];
-  double g2 = 2.0 * d.cq[g];
+  double g1 = fs * (2.0 * d.cq[g] * p + d.cl[g]);
+  double g2 = fs * 2.0 * d.cq[g];
   double lp, up, lq, uq;
   box_shift(d.pmin[g], d.pmax[g], p, delta, lp, up);
   box_shift(d.qmin[g], d.qmax[g], q, delta, lq, uq);
@@ -363,11 +385,11 @@ __global__ void k_build_gen(Dev d, double* xgen) {
 
 // buses: p_i^{d,(k)}, q_i^{d,(k)} (CSR gather of the branch flows at the bus)
 template <typename T>
-__global__ void k_build_bus(Dev d, double* xbus) {
+__global__ void k_build_bus(Dev d, double* xbus, int pass) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.B) return;
   int k = d.bus_inst[i];
-  if (d.ctl[k].result != ACOPF_RUNNING) return;
+  if (!live(d.ctl[k], pass)) return;
   double pk = d.pd[i] + d.gs[i] * d.w[i];
   double qk = d.qd[i] - d.bs[i] * d.w[i];
   for (int g = d.gen_ptr[i]; g < d.gen_ptr[i + 1]; ++g) {
@@ -393,11 +415,11 @@ __global__ void k_build_bus(Dev d, double* xbus) {
 // recovered from the KKT conditions of each line subproblem (Sec. IV-B):
 // pi13, pi14 = -(line-limit multipliers); (pi11, pi12) from stationarity in (d_wR, d_wI).
 template <typename T>
-__global__ void k_step_branch(Dev d) {
+__global__ void k_step_branch(Dev d, int pass) {
   int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= d.L) return;
   int k = d.br_inst[l];
-  if (d.ctl[k].result != ACOPF_RUNNING) return;
+  if (!live(d.ctl[k], pass)) return;
   Br b;
   load_branch(d, l, b);
   const V2<T>* ZB = (const V2<T>*)d.ZB;
@@ -462,11 +484,11 @@ __global__ void k_step_branch(Dev d) {
 }
 
 template <typename T>
-__global__ void k_step_nodes(Dev d) {
+__global__ void k_step_nodes(Dev d, int pass) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n < d.G) {
     int k = d.gen_inst[n];
-    if (d.ctl[k].result == ACOPF_RUNNING) {
+    if (live(d.ctl[k], pass)) {
       V2<T> xg = ((const V2<T>*)d.XG)[n];
       d.dpg[n] = (double)xg.x;
       d.dqg[n] = (double)xg.y;
@@ -474,7 +496,7 @@ __global__ void k_step_nodes(Dev d) {
   }
   if (n < d.B) {
     int k = d.bus_inst[n];
-    if (d.ctl[k].result == ACOPF_RUNNING) {
+    if (live(d.ctl[k], pass)) {
       V2<T> zb = ((const V2<T>*)d.ZB)[n];
       d.dw[n] = (double)zb.x;
       d.dth[n] = (double)zb.y;
@@ -497,11 +519,11 @@ __device__ __forceinline__ void angle_viol(double th, double amin, double amax, 
   if (amax < kTwoPi) { double v = negpart(amax - th); s += v; m = fmax(m, v); }
 }
 
-__global__ void k_merit_branch(Dev d, int use_angle) {
+__global__ void k_merit_branch(Dev d, int use_angle, int pass) {
   int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= d.L) return;
   int k = d.br_inst[l];
-  if (d.ctl[k].result != ACOPF_RUNNING) return;
+  if (!live(d.ctl[k], pass)) return;
   Br b;
   load_branch(d, l, b);
   double zs[6] = {d.dw[b.i], d.dth[b.i], d.dwr[l], d.dwi[l], d.dw[b.j], d.dth[b.j]};
@@ -566,11 +588,11 @@ __global__ void k_merit_branch(Dev d, int use_angle) {
   t[6 * L + l] = mx;
 }
 
-__global__ void k_merit_bus(Dev d) {
+__global__ void k_merit_bus(Dev d, int pass) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.B) return;
   int k = d.bus_inst[i];
-  if (d.ctl[k].result != ACOPF_RUNNING) return;
+  if (!live(d.ctl[k], pass)) return;
   double w0 = d.w[i], w1 = d.w[i] + d.dw[i];
   double t0 = d.th[i], t1 = d.th[i] + d.dth[i];
   double p0 = -d.pd[i] - d.gs[i] * w0, q0 = -d.qd[i] + d.bs[i] * w0;
@@ -606,11 +628,11 @@ __global__ void k_merit_bus(Dev d) {
   d.tbus[2 * d.B + i] = mx;
 }
 
-__global__ void k_merit_gen(Dev d) {
+__global__ void k_merit_gen(Dev d, int pass) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= d.G) return;
   int k = d.gen_inst[g];
-  if (d.ctl[k].result != ACOPF_RUNNING) return;
+  if (!live(d.ctl[k], pass)) return;
   double p0 = d.pg[g], q0 = d.qg[g];
   double p1 = p0 + d.dpg[g], q1 = q0 + d.dqg[g];
   double h0 = negpart(p0 - d.pmin[g]) + negpart(d.pmax[g] - p0) + negpart(q0 - d.qmin[g]) + negpart(d.qmax[g] - q0);
@@ -652,11 +674,21 @@ __device__ void seg_reduce(const double* t, int n, int beg, int end, const int* 
   __syncthreads();
 }
 
-// l1 merit acceptance (Sec. II-C) and trust-region update (Alg. 1, acceptance and radius rules)
-__global__ void __launch_bounds__(256) k_decide(Dev d) {
+// the ratio test of Sec. II-C: ared > 0 and ared / pred > 0
+__device__ __forceinline__ bool ratio_ok(double ared, double pred) {
+  return isfinite(ared) && isfinite(pred) && ared > 0 && pred > 0;
+}
+
+// l1 merit acceptance (Sec. II-C) and trust-region update (Alg. 1, acceptance
+// and radius rules).  Main pass (0): the QP step d.  When d fails the test and
+// second-order correction is on (with a positive model reduction), the
+// decision waits for the correction pass (1), which judges the corrected step
+// against d's model reduction; the radius rule then uses the accepted step's
+// norm, or d's on rejection.
+__global__ void __launch_bounds__(256) k_decide(Dev d, int pass) {
   int k = blockIdx.x;
   InstCtl& c = d.ctl[k];
-  if (c.result != ACOPF_RUNNING) return;
+  if (!live(c, pass)) return;
   __shared__ double rb[7], rbus[3], rg[7];
   const int opb[7] = {0, 0, 0, 0, 0, 0, 1};
   const int opbus[3] = {0, 0, 1};
@@ -665,7 +697,11 @@ __global__ void __launch_bounds__(256) k_decide(Dev d) {
   seg_reduce<3>(d.tbus, d.B, d.bus_off[k], d.bus_off[k + 1], opbus, rbus);
   seg_reduce<7>(d.tgen, d.G, d.gen_off[k], d.gen_off[k + 1], opg, rg);
   if (threadIdx.x != 0) return;
-  c.admm_iter_last = d.admm_iters[k];
+  if (pass == 0) {
+    c.admm_iter_last = d.admm_iters[k];
+  } else {
+    c.admm_iter_last += d.admm_iters[k];
+  }
   c.admm_iter_total += d.admm_iters[k];
   c.r_inf = d.admm_rs[k];
   c.s_inf = d.admm_rs[d.K + k];
@@ -675,17 +711,43 @@ __global__ void __launch_bounds__(256) k_decide(Dev d) {
   double h0 = rb[0] + wl * (rb[1] + rbus[0] + rg[0]);
   double lin1 = wl * (rb[3] + rbus[1] + rg[1]);     // linear constraints at x + d
   double h1 = rb[2] + lin1;
+  const double fs = c.fscale;                        // objective weight (0 while restoring)
   double f0 = rg[2], f1 = rg[3];
-  double phx = f0 + mu * h0, phxd = f1 + mu * h1;
+  double phx = fs * f0 + mu * h0, phxd = fs * f1 + mu * h1;
   double md = rb[5] + lin1;
   double pred = -rg[4] - 0.5 * (rg[5] + rb[4]) + mu * (h0 - md);
   double ared = phx - phxd;
   // step norm over the trust-region variables (pg, qg, w, theta)
   double dn = d.red[16 * k + 0];
-  int accept = isfinite(ared) && isfinite(pred) && ared > 0 && pred > 0;
-  if (c.sqp_iter == 0) {  // objective and infeasibility of the starting point
+  if (c.sqp_iter == 0 && pass == 0) {  // objective and infeasibility of the starting point
     c.obj = f0;
     c.primal = fmax(fmax(rb[6], rbus[2]), rg[6]);
+  }
+  int accept;
+  if (pass == 0) {
+    accept = ratio_ok(ared, pred);
+    c.soc_flag = 0;
+    if (!accept && c.soc_on && isfinite(pred) && pred > 0) {
+      c.soc_active = 1;
+      c.phx_saved = phx;
+      c.pred_saved = pred;
+      c.dn_saved = dn;
+      c.ared_saved = ared;
+      return;  // decided by the correction pass
+    }
+  } else {
+    // the corrected step: merit at x + d' against the original model reduction
+    const double ared2 = c.phx_saved - phxd;
+    pred = c.pred_saved;
+    c.soc_active = 0;
+    accept = ratio_ok(ared2, pred);
+    c.soc_flag = accept ? 2 : 1;
+    if (accept) {
+      ared = ared2;
+    } else {
+      ared = c.ared_saved;
+      dn = c.dn_saved;
+    }
   }
   c.ared = ared;
   c.pred = pred;
@@ -703,9 +765,9 @@ __global__ void __launch_bounds__(256) k_decide(Dev d) {
 }
 
 // l_inf norm of the step over (pg, qg, w, theta), per instance
-__global__ void __launch_bounds__(256) k_step_norm(Dev d) {
+__global__ void __launch_bounds__(256) k_step_norm(Dev d, int pass) {
   int k = blockIdx.x;
-  if (d.ctl[k].result != ACOPF_RUNNING) return;
+  if (!live(d.ctl[k], pass)) return;
   __shared__ double sh[256];
   double m = 0;
   for (int g = d.gen_off[k] + threadIdx.x; g < d.gen_off[k + 1]; g += blockDim.x)
@@ -857,17 +919,46 @@ __global__ void __launch_bounds__(256) k_kkt_decide(Dev d) {
   if (threadIdx.x != 0) return;
   if (c.accept_last) c.dual = fmax(fmax(a[0], bsh[0]), gg[1]) / fmax(1.0, gg[0]);
   if (c.sqp_iter >= 1 && c.sqp_iter <= ACOPF_HIST_MAX) {
-    double* hr = d.hist + ((size_t)k * ACOPF_HIST_MAX + (c.sqp_iter - 1)) * 12;
+    double* hr = d.hist + ((size_t)k * ACOPF_HIST_MAX + (c.sqp_iter - 1)) * kHistW;
     hr[0] = c.obj; hr[1] = c.primal; hr[2] = c.dual; hr[3] = c.admm_iter_last;
     hr[4] = c.r_inf; hr[5] = c.s_inf; hr[6] = c.accept_last; hr[7] = c.delta;
     hr[8] = c.dnorm; hr[9] = c.ared; hr[10] = c.pred; hr[11] = d.rho_fac[k];
+    hr[12] = c.soc_flag; hr[13] = c.restoring;
   }
+  // no progress towards feasibility: the infeasibility, above 10 tol, has not
+  // fallen by a tenth over the last five iterations (of the current phase)
+  const int it = c.sqp_iter - 1;
+  const double older = c.primal_ring[it % 5];
+  c.primal_ring[it % 5] = c.primal;
+  const bool no_progress = it >= 5 && c.primal > 10 * c.tol && c.primal > 0.9 * older && c.since_switch >= 5;
+  c.since_switch += 1;
+  const bool stall = (c.accept_last && c.dnorm <= c.step_tol) || c.delta < c.delta_min;
   if (!isfinite(c.obj) || !isfinite(c.primal) || !isfinite(c.dual) || !isfinite(c.delta)) {
     c.result = ACOPF_NONFINITE;
-  } else if (c.accept_last && c.primal <= c.tol && c.dual <= c.tol) {
-    c.result = ACOPF_CONVERGED;
-  } else if ((c.accept_last && c.dnorm <= c.step_tol) || c.delta < c.delta_min) {
-    c.result = ACOPF_STEP_TOO_SMALL;
+  } else if (!c.restoring) {
+    if (c.accept_last && c.primal <= c.tol && c.dual <= c.tol) {
+      c.result = ACOPF_CONVERGED;
+    } else if (stall || (c.restore_on && no_progress)) {
+      if (c.restore_on && c.primal > c.tol) {
+        // feasibility restoration: the violation alone (objective weight 0,
+        // merit mu h) from the current point and radius delta0
+        c.restoring = 1;
+        c.fscale = 0.0;
+        c.delta = c.delta0;
+        c.since_switch = 0;
+      } else {
+        c.result = ACOPF_STEP_TOO_SMALL;
+      }
+    }
+  } else {
+    if (c.accept_last && c.primal <= c.tol) {  // feasible again: back to the SQP on the ACOPF
+      c.restoring = 0;
+      c.fscale = 1.0;
+      c.delta = c.delta0;
+      c.since_switch = 0;
+    } else if (stall || no_progress) {
+      c.result = ACOPF_INFEASIBLE;  // the violation stalls above tol: locally infeasible
+    }
   }
 }
 
@@ -978,42 +1069,42 @@ void launch_fill_rho(Ctx& c, double rho) {
   c.launches++;
 }
 
-void launch_build(Ctx& c, bool do_export) {
+void launch_build(Ctx& c, bool do_export, int pass) {
   Dev& d = c.d;
   double* xb = do_export ? d.xbr : nullptr;
   double* xg = do_export ? d.xgen : nullptr;
   double* xs = do_export ? d.xbus : nullptr;
   if (c.precision == ACOPF_MIXED) {
-    k_build_branch<float><<<nblk(d.L, 128), 128, 0, c.stream>>>(d, c.use_angle, xb);
-    k_build_gen<float><<<nblk(d.G, 256), 256, 0, c.stream>>>(d, xg);
-    k_build_bus<float><<<nblk(d.B, 256), 256, 0, c.stream>>>(d, xs);
+    k_build_branch<float><<<nblk(d.L, 128), 128, 0, c.stream>>>(d, c.use_angle, xb, pass);
+    k_build_gen<float><<<nblk(d.G, 256), 256, 0, c.stream>>>(d, xg, pass);
+    k_build_bus<float><<<nblk(d.B, 256), 256, 0, c.stream>>>(d, xs, pass);
   } else {
-    k_build_branch<double><<<nblk(d.L, 128), 128, 0, c.stream>>>(d, c.use_angle, xb);
-    k_build_gen<double><<<nblk(d.G, 256), 256, 0, c.stream>>>(d, xg);
-    k_build_bus<double><<<nblk(d.B, 256), 256, 0, c.stream>>>(d, xs);
+    k_build_branch<double><<<nblk(d.L, 128), 128, 0, c.stream>>>(d, c.use_angle, xb, pass);
+    k_build_gen<double><<<nblk(d.G, 256), 256, 0, c.stream>>>(d, xg, pass);
+    k_build_bus<double><<<nblk(d.B, 256), 256, 0, c.stream>>>(d, xs, pass);
   }
   c.launches += 3;
 }
 
-void launch_step(Ctx& c) {
+void launch_step(Ctx& c, int pass) {
   Dev& d = c.d;
   if (c.precision == ACOPF_MIXED) {
-    k_step_branch<float><<<nblk(d.L, 128), 128, 0, c.stream>>>(d);
-    k_step_nodes<float><<<cover(d), 256, 0, c.stream>>>(d);
+    k_step_branch<float><<<nblk(d.L, 128), 128, 0, c.stream>>>(d, pass);
+    k_step_nodes<float><<<cover(d), 256, 0, c.stream>>>(d, pass);
   } else {
-    k_step_branch<double><<<nblk(d.L, 128), 128, 0, c.stream>>>(d);
-    k_step_nodes<double><<<cover(d), 256, 0, c.stream>>>(d);
+    k_step_branch<double><<<nblk(d.L, 128), 128, 0, c.stream>>>(d, pass);
+    k_step_nodes<double><<<cover(d), 256, 0, c.stream>>>(d, pass);
   }
   c.launches += 2;
 }
 
-void launch_merit(Ctx& c) {
+void launch_merit(Ctx& c, int pass) {
   Dev& d = c.d;
-  k_merit_branch<<<nblk(d.L, 128), 128, 0, c.stream>>>(d, c.use_angle);
-  k_merit_bus<<<nblk(d.B, 256), 256, 0, c.stream>>>(d);
-  k_merit_gen<<<nblk(d.G, 256), 256, 0, c.stream>>>(d);
-  k_step_norm<<<d.K, 256, 0, c.stream>>>(d);
-  k_decide<<<d.K, 256, 0, c.stream>>>(d);
+  k_merit_branch<<<nblk(d.L, 128), 128, 0, c.stream>>>(d, c.use_angle, pass);
+  k_merit_bus<<<nblk(d.B, 256), 256, 0, c.stream>>>(d, pass);
+  k_merit_gen<<<nblk(d.G, 256), 256, 0, c.stream>>>(d, pass);
+  k_step_norm<<<d.K, 256, 0, c.stream>>>(d, pass);
+  k_decide<<<d.K, 256, 0, c.stream>>>(d, pass);
   c.launches += 5;
 }
 

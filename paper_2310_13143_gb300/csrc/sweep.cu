@@ -948,13 +948,13 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && !RES) ? 2 : 1) k_sweep
 // ADMM state reset: d = 0, z = 0 (and lambda = 0 unless kept); instances that
 // are no longer running keep their state
 template <typename T>
-__global__ void k_admm_reset(Dev d, int keep_lambda) {
+__global__ void k_admm_reset(Dev d, int keep_lambda, int pass) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   V4<T> z4 = {T(0), T(0), T(0), T(0)};
   V2<T> z2 = {T(0), T(0)};
   if (n < 2 * d.L) {
     int k = d.br_inst[n >> 1];
-    if (d.ctl[k].result == ACOPF_RUNNING) {
+    if (live(d.ctl[k], pass)) {
       ((V4<T>*)d.X)[n] = z4;
       ((V4<T>*)d.Z)[n] = z4;
       if (!keep_lambda) ((V4<T>*)d.LAM)[n] = z4;
@@ -963,7 +963,7 @@ __global__ void k_admm_reset(Dev d, int keep_lambda) {
   }
   if (n < d.G) {
     int k = d.gen_inst[n];
-    if (d.ctl[k].result == ACOPF_RUNNING) {
+    if (live(d.ctl[k], pass)) {
       ((V2<T>*)d.XG)[n] = z2;
       ((V2<T>*)d.ZG)[n] = z2;
       if (!keep_lambda) ((V2<T>*)d.LG)[n] = z2;
@@ -971,13 +971,13 @@ __global__ void k_admm_reset(Dev d, int keep_lambda) {
   }
   if (n < d.B) {
     int k = d.bus_inst[n];
-    if (d.ctl[k].result == ACOPF_RUNNING) {
+    if (live(d.ctl[k], pass)) {
       ((V2<T>*)d.ZB)[n] = z2;
       ((V2<T>*)d.NU)[n] = z2;
     }
   }
   if (n < d.K) {
-    d.admm_done[n] = d.ctl[n].result == ACOPF_RUNNING ? 0 : 1;
+    d.admm_done[n] = live(d.ctl[n], pass) ? 0 : 1;
     d.admm_iters[n] = 0;
   }
 }
@@ -1126,16 +1126,16 @@ acopf_status launch_sweep(Ctx& c, const admm_options& o, int fixed_iters) {
   return c.precision == ACOPF_MIXED ? run_sweep<float>(c, o, fixed_iters) : run_sweep<double>(c, o, fixed_iters);
 }
 
-void launch_admm_reset(Ctx& c, int keep_lambda) {
+void launch_admm_reset(Ctx& c, int keep_lambda, int pass) {
   Dev& d = c.d;
   long m = 2L * d.L;
   if (d.G > m) m = d.G;
   if (d.B > m) m = d.B;
   if (d.K > m) m = d.K;
   if (c.precision == ACOPF_MIXED)
-    k_admm_reset<float><<<nblk(m, 256), 256, 0, c.stream>>>(d, keep_lambda);
+    k_admm_reset<float><<<nblk(m, 256), 256, 0, c.stream>>>(d, keep_lambda, pass);
   else
-    k_admm_reset<double><<<nblk(m, 256), 256, 0, c.stream>>>(d, keep_lambda);
+    k_admm_reset<double><<<nblk(m, 256), 256, 0, c.stream>>>(d, keep_lambda, pass);
   c.launches++;
 }
 
