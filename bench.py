@@ -130,13 +130,15 @@ class Clocks:
 MAX_SQP = 20  # the paper's runs need at most 18 SQP iterations (Sec. V); instances that converge here need <= 16
 
 
-def solver_options(binding, precision):
+def solver_options(binding, precision, soc=0, restore=0):
     """SQP tolerance 1e-4, at most MAX_SQP iterations; ADMM with the paper's
     large-case settings (rho 2e4, 1,000 iterations, eps 1e-3; Table II); the
     FP32 sweep's dual residual is tested against 5e-3 (its floor is rho times
-    the FP32 resolution of z)."""
-    return binding.default_sqp(tol=1e-4, max_sqp=MAX_SQP, admm=dict(rho=2e4, max_iter=1000, eps=1e-3,
-                                                                    eps_dual=5e-3 if precision == "mixed" else 0.0))
+    the FP32 resolution of z).  soc, restore: second-order correction and
+    feasibility restoration (off for the paper's plain method)."""
+    return binding.default_sqp(tol=1e-4, max_sqp=MAX_SQP, soc=soc, restore=restore,
+                               admm=dict(rho=2e4, max_iter=1000, eps=1e-3,
+                                         eps_dual=5e-3 if precision == "mixed" else 0.0))
 
 
 def headline_config(grid, precision, world):
@@ -326,6 +328,10 @@ def run_gpu(args, rank, world, local_rank):
                              "objective": plain["obj"], "objective_rel_diff_vs_mixed": abs(plain["obj"] - m["obj"]) / abs(plain["obj"]),
                              "avg_sweep_launch_ms": plain["prof"]["sweep_ms"] / max(plain["prof"]["sweeps"], 1)}
         summary["plain_fp64_solves_s"] = round(out["plain_fp64"]["value"], 3)
+    if world == 1 and not args.no_small:
+        sm = small_30bus()
+        out["small_30bus"] = sm
+        summary["small_30bus"] = {"solves_s": round(sm["value"], 1), "oracle_solves_s": round(sm["oracle"]["value"], 1)}
     if world == 1 and not args.no_rho_sweep:
         out["rho_sweep"] = rho_sweep(grid, args.precision)
         summary["rho_sweep_solves_s"] = {f"{r['rho']:g}": round(r["solves_per_s"], 2) for r in out["rho_sweep"]}
@@ -349,7 +355,8 @@ def run_gpu(args, rank, world, local_rank):
         summary["batched_sweep"] = {"us_iter": round(bs["us_per_iter"], 1), "frac": round(bs["roofline"]["frac"], 3),
                                     "layout_frac": round(bs["roofline"]["layout_frac"], 3)}
         summary["batched_solve"] = {"solves_s": round(bsol["value"], 1), "conv": bsol["converged"],
-                                    "of": bsol["instances"], "s": round(bsol["seconds"], 3),
+                                    "of": bsol["instances"], "uneven": bsol["outcomes"]["uneven"],
+                                    "s": round(bsol["seconds"], 3),
                                     "plain_est_s": round(bsol["plain_fp64_sample"]["estimated_seconds_all"], 1),
                                     "vs_plain": round(bsol["batched_vs_plain"], 1),
                                     "MB": round(bsol["device_bytes"] / 2 ** 20)}
@@ -379,6 +386,50 @@ def run_gpu(args, rank, world, local_rank):
     # truncated record keeps): compact, last
     out["summary"] = summary
     return out
+
+
+def small_30bus(reps=20):
+    """The synthetic 30-bus grid (the first workload): plain FP64 solves on the
+    GPU, one handle, from the flat start to 1e-4 with the solver's default
+    ADMM settings (rho 2e4, eps 1e-4), against the oracle's single-thread
+    solves of the same grid and settings."""
+    import torch
+
+    import oracle
+    from paper_2310_13143_gb300 import binding, gridgen
+
+    g = gridgen.grid_30bus()
+    opts = binding.default_sqp(tol=1e-4, max_sqp=30)
+    stream = torch.cuda.Stream()
+    s = binding.Solver(g, precision="fp64")
+    s.set_stream(stream.cuda_stream)
+    s.sqp_solve(opts)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    conv = 0
+    a.record(stream)
+    for _ in range(reps):
+        s.sqp_solve(opts)
+        r = s.get_residuals(0)
+        conv += int(r["result_name"] == "converged" and r["primal"] <= 1e-4 and r["dual"] <= 1e-4)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    obj = s.get_solution(0)["obj"]
+    s.close()
+    oracle.build()
+    m = oracle.Model(g)
+    t0 = time.perf_counter()
+    n = oconv = 0
+    while n < 3 or time.perf_counter() - t0 < 2.0:
+        ro = m.sqp(oracle.SqpOptions(tol=1e-4, max_sqp=30))
+        oconv += int(_oracle_converged(ro))
+        n += 1
+    to = time.perf_counter() - t0
+    return {"workload": "synthetic 30-bus grid (41 branches, 6 generators), FP64, default ADMM settings",
+            "value": conv / t, "unit": "solves/s", "ms_per_solve": 1e3 * t / reps, "converged": conv, "of": reps,
+            "sqp_iters": r["sqp_iter"], "admm_iters": r["admm_iter"], "objective": obj,
+            "objective_rel_diff_vs_oracle": abs(obj - ro["obj"]) / abs(ro["obj"]),
+            "oracle": {"value": oconv / to, "unit": "solves/s", "cores": 1, "solves": n}}
 
 
 def rho_sweep(grid, precision, rhos=(2e3, 5e3, 1e4, 2e4, 5e4), reps=3):
@@ -424,7 +475,9 @@ def batched_solve(grids, nscen=256, stride=10):
 
     from paper_2310_13143_gb300 import binding
 
-    opts = solver_options(binding, "mixed")
+    # second-order correction and feasibility restoration on: stalled instances
+    # end early, certified locally infeasible
+    opts = solver_options(binding, "mixed", soc=1, restore=1)
     stream = torch.cuda.Stream()
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
@@ -443,10 +496,14 @@ def batched_solve(grids, nscen=256, stride=10):
     t = e0.elapsed_time(e1) / 1e3
     rs = [s.get_residuals(k) for k in range(len(grids))]
     ok = [r["result_name"] == "converged" and r["primal"] <= 1e-4 and r["dual"] <= 1e-4 for r in rs]
+    outcomes = {}
+    for part, sl in (("scenarios", slice(0, nscen)), ("uneven", slice(nscen, None))):
+        names = [r["result_name"] for r in rs[sl]]
+        outcomes[part] = {n: names.count(n) for n in sorted(set(names))}
     s.close()
-    # plain: one handle per sampled instance, cold, FP64
+    # plain: one handle per sampled instance, cold, FP64, the same SQP options
     idx = list(range(0, len(grids), stride))
-    popts = solver_options(binding, "fp64")
+    popts = solver_options(binding, "fp64", soc=1, restore=1)
     times = {"scenario": [], "uneven": []}
     pconv = 0
     for i in idx:
@@ -470,6 +527,7 @@ def batched_solve(grids, nscen=256, stride=10):
             "sqp_iters_max": max(r["sqp_iter"] for r in rs),
             "admm_iters_mean": float(sum(r["admm_iter"] for r in rs) / len(rs)),
             "converged_scenarios": int(sum(ok[:nscen])), "converged_uneven": int(sum(ok[nscen:])),
+            "outcomes": outcomes,
             "launch_shape": {"block_threads": shape[0], "ctas_per_sm": shape[1], "stages": shape[2],
                              "tuned_us_per_iter": tune_us},
             "device_bytes": int(footprint),
@@ -480,7 +538,8 @@ def batched_solve(grids, nscen=256, stride=10):
                                   "estimate": "per kind: instances in the batch x mean sampled plain time"},
             "batched_vs_plain": est / t if t > 0 else None,
             "workload": "256 correlated load scenarios of the 2,000-bus grid + 64 grids of 118-10,000 buses, "
-                        f"one handle, SQP to 1e-4 (max {MAX_SQP} SQP iterations, 1,000 ADMM iterations per QP)"}
+                        f"one handle, SQP to 1e-4 (max {MAX_SQP} SQP iterations, 1,000 ADMM iterations per QP), "
+                        "second-order correction and feasibility restoration on"}
 
 
 def learned_warm_start(args, ntrain=4096, ntest=512, steps=6000, batch=256, lr=3e-3, rho_steps=1500, rho_lr=1e-3):
@@ -697,8 +756,8 @@ def large_solve(grids, tol=1e-3, max_iter=1000):
     s = binding.Solver(grids, precision="mixed")
     s.set_stream(stream.cuda_stream)
     s.autotune(os.path.join(tempfile.gettempdir(), "acopf_tune_cache.json"), iters=30)
-    opts = binding.default_sqp(tol=tol, max_sqp=MAX_SQP, admm=dict(rho=2e4, max_iter=max_iter, eps=1e-3,
-                                                                   eps_dual=5e-3))
+    opts = binding.default_sqp(tol=tol, max_sqp=MAX_SQP, soc=1, restore=1,
+                               admm=dict(rho=2e4, max_iter=max_iter, eps=1e-3, eps_dual=5e-3))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     s.sqp_solve_graph(opts, check_every=2)
@@ -713,9 +772,12 @@ def large_solve(grids, tol=1e-3, max_iter=1000):
            "sqp_iters": [r["sqp_iter"] for r in rs], "admm_iters_mean": float(sum(r["admm_iter"] for r in rs) / len(rs)),
            "primal_median": primal[len(primal) // 2], "primal_max": primal[-1],
            "dual_max": max(r["dual"] for r in rs), "results": sorted({r["result_name"] for r in rs}),
-           "settings": f"rho 2e4, {max_iter} ADMM iterations per QP, eps 1e-3 (dual 5e-3), at most {MAX_SQP} SQP"}
+           "settings": f"rho 2e4, {max_iter} ADMM iterations per QP, eps 1e-3 (dual 5e-3), at most {MAX_SQP} SQP, "
+                       "second-order correction and feasibility restoration on"}
+    names = [r["result_name"] for r in rs]
+    out["outcomes"] = {n: names.count(n) for n in sorted(set(names))}
     out["summary"] = {"conv": out["converged"], "of": len(grids), "tol": tol, "s": round(t, 2),
-                      "primal_med": float(f"{out['primal_median']:.2e}")}
+                      "primal_med": float(f"{out['primal_median']:.2e}"), "outcomes": out["outcomes"]}
     return out
 
 
@@ -936,6 +998,7 @@ def main():
     ap.add_argument("--no-rho-sweep", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-large-solve", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--workload", default="syn2000",
                     choices=["syn2000", "batched", "syn70k", "syn70k_x16", "gemm", "mlp_train"])
     ap.add_argument("--gemm-shape", default="8192,8192,8192")
