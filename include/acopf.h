@@ -168,7 +168,8 @@ acopf_status acopf_last_error(acopf_handle h, char* buf, size_t n);
  * solver state.  Instances are solved together by every later call.
  * Errors: EINVAL for an index out of range, x <= 0 with r = 0, vmin > vmax,
  * pmin > pmax, qmin > qmax, no (or more than one) reference bus, an isolated
- * bus, or ngrids < 1; ECUDA without a device. */
+ * bus, ngrids < 1, or more components than 32-bit indices hold (all buses,
+ * or 2 x branches + generators, at 2^30 or more); ECUDA without a device. */
 acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_options* opt,
                           acopf_handle* out);
 acopf_status acopf_destroy(acopf_handle h);

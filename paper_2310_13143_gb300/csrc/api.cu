@@ -268,6 +268,16 @@ acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_o
       return ACOPF_EINVAL;
     }
   }
+  {
+    // component indices are 32-bit: branch ends (2L) and bus-update entries
+    // (G + 2L) must stay below 2^30
+    long long b = 0, l = 0, gg = 0;
+    for (int k = 0; k < ngrids; ++k) { b += grids[k].nbus; l += grids[k].nbranch; gg += grids[k].ngen; }
+    if (b >= (1ll << 30) || 2 * l + gg >= (1ll << 30)) {
+      g_create_error = "acopf_create: too many components for 32-bit indices (buses, 2 x branches + generators < 2^30)";
+      return ACOPF_EINVAL;
+    }
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1 || o.device < 0 || o.device >= ndev) {
     cudaGetLastError();
