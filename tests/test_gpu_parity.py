@@ -311,9 +311,12 @@ def test_autotune_applies_and_caches_a_shape(tmp_path):
 
 def test_mixed_sweep_launch_shapes_agree():
     """The FP32 sweep reads branch records from shared-memory tiles (one or two
-    buffers), in place from global memory, or once into registers, with any
-    CTA size: the same arithmetic on the same values, so the state after a
-    fixed number of iterations must be identical."""
+    buffers) or in place from global memory, with any CTA size: the same
+    arithmetic on the same values, so the state after a fixed number of
+    iterations must be identical.  The resident form (records held in
+    registers) is a separately compiled kernel in which the compiler may
+    contract multiply-adds differently: it must agree to 1e-4 of each
+    array's scale (FP32 rounding carried over 25 iterations)."""
     grids = [gg.geometric_grid(118, seed=7), gg.grid_30bus(), gg.hub_grid(40)]
     ref = None
     for bt, st in [(256, 1), (256, 0), (128, 2), (64, 0), (96, 1), (256, 3), (64, 3), (32, 3)]:
@@ -328,7 +331,12 @@ def test_mixed_sweep_launch_shapes_agree():
             continue
         for a, b in zip(ref, got):
             for key in ("x", "z", "lam", "xg", "zg", "lg", "zb", "nu", "ul"):
-                np.testing.assert_array_equal(a[key], b[key], err_msg=f"{bt}:{st}:{key}")
+                if st == 3:
+                    # a kernel of its own: the compiler may fuse multiply-adds differently there
+                    np.testing.assert_allclose(a[key], b[key], rtol=0, atol=1e-4 * max(1.0, np.abs(a[key]).max()),
+                                               err_msg=f"{bt}:{st}:{key}")
+                else:
+                    np.testing.assert_array_equal(a[key], b[key], err_msg=f"{bt}:{st}:{key}")
 
 
 @pytest.mark.parametrize("name", ["syn30", "syn30_shunt_tap", "syn118", "hub41", "two_bus"])
@@ -359,7 +367,8 @@ def test_linear_projection_matches_oracle(name):
 
 def test_fp64_sweep_resident_records_agree():
     """The FP64 sweep with records held in registers gives the same state as
-    with records read in place."""
+    with records read in place, to the rounding of a separately compiled
+    kernel (1e-9 of each array's scale)."""
     grids = [gg.geometric_grid(118, seed=7), gg.grid_30bus(), gg.hub_grid(40)]
     ref = None
     for bt, st in [(256, 0), (256, 3), (64, 3)]:
@@ -374,4 +383,8 @@ def test_fp64_sweep_resident_records_agree():
             continue
         for a, b in zip(ref, got):
             for key in a:
-                np.testing.assert_array_equal(a[key], b[key], err_msg=f"{key} threads {bt} mode {st}")
+                if st == 3:
+                    np.testing.assert_allclose(a[key], b[key], rtol=0, atol=1e-9 * max(1.0, np.abs(a[key]).max()),
+                                               err_msg=f"{key} threads {bt} mode {st}")
+                else:
+                    np.testing.assert_array_equal(a[key], b[key], err_msg=f"{key} threads {bt} mode {st}")
