@@ -360,7 +360,12 @@ acopf_status acopf_get_profile_phases(acopf_handle h, double* ns);
  * per sweep into registers, together with every other piece of static data
  * (instance ids, bus-task slots, bus loads), which needs a co-resident grid
  * with one thread per generator or branch and at most two bus tasks per
- * warp, and residual balancing off -- otherwise the sweep runs as with 0. */
+ * warp, and residual balancing off -- otherwise the sweep runs as with 0;
+ * 4 = one thread-block cluster of up to 16 CTAs per instance (enough CTAs
+ * for one thread per generator or branch of the largest instance), whose
+ * barriers are the cluster's hardware barrier and whose residual maxima are
+ * combined in distributed shared memory, so instances never wait on one
+ * another (residual balancing off -- otherwise as with 0). */
 acopf_status acopf_tune(acopf_handle h, int32_t block_threads, int32_t ctas_per_sm, int32_t sweep_stages);
 
 /* Autotuner of the sweep's launch shape.  If cache_path (may be NULL) names a
@@ -368,8 +373,8 @@ acopf_status acopf_tune(acopf_handle h, int32_t block_threads, int32_t ctas_per_
  * precision and the binary orders of magnitude of the instance, bus and
  * branch counts -- that shape is applied.  Otherwise the QP at the current
  * iterate is built (delta 1, rho 2e4) and every shape of {64, 128, 256}
- * threads x {as many CTAs per SM as fit, 1} x record access {0, 1, 2, 3}
- * (FP32 sweep; FP64: {0, 3}, see acopf_tune) is timed over iters fixed ADMM iterations with CUDA
+ * threads x {as many CTAs per SM as fit, 1} x record access {0, 1, 2, 3, 4}
+ * (FP32 sweep; FP64: {0, 3, 4}, see acopf_tune) is timed over iters fixed ADMM iterations with CUDA
  * events; the fastest is applied and written to the cache (other keys are
  * kept).  shape_out (3 ints: threads, CTAs per SM, buffers) and us_per_iter
  * (-1 when taken from the cache) may be NULL.  Resets the ADMM state: call it

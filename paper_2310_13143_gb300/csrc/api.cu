@@ -375,7 +375,7 @@ acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_o
   // bus update work list and its warp tasks (consecutive whole buses, at most
   // 32 entries per task; a bus with more entries is a task of its own)
   const size_t E = (size_t)G + 2 * (size_t)L;
-  std::vector<int> ent(E), ebus(E), pent, pbus, pinst, big;
+  std::vector<int> ent(E), ebus(E), pent, pbus, pinst, big, task_off, big_off;
   {
     size_t q = 0;
     for (int i = 0; i < B; ++i) {
@@ -395,7 +395,17 @@ acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_o
       q0 += cnt;
       cnt = 0;
     };
+    task_off.assign(K + 1, 0);
+    big_off.assign(K + 1, 0);
+    int kk = 0;
     for (int i = 0; i < B; ++i) {
+      // tasks never span two instances (a cluster of the sweep takes whole tasks of its instance)
+      while (kk < K && i == bus_off[kk]) {
+        close();
+        task_off[kk] = (int)(pbus.size() / 32);
+        big_off[kk] = (int)(big.size() / 2);
+        ++kk;
+      }
       size_t n = (size_t)(gen_ptr[i + 1] - gen_ptr[i]) + (size_t)(end_ptr[i + 1] - end_ptr[i]);
       if (n > 32) {
         close();
@@ -408,6 +418,10 @@ acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_o
       cnt += n;
     }
     close();
+    for (; kk <= K; ++kk) {
+      task_off[kk] = (int)(pbus.size() / 32);
+      big_off[kk] = (int)(big.size() / 2);
+    }
   }
 
   // ---- device allocation
@@ -421,7 +435,7 @@ acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_o
   A(d.pd, B); A(d.qd, B); A(d.gs, B); A(d.bs, B); A(d.wmin, B); A(d.wmax, B); A(d.isref, B);
   A(d.end_ptr, B + 1); A(d.end_idx, 2 * (size_t)L); A(d.gen_ptr, B + 1);
   A(d.ent, E); A(d.ebus, E); A(d.pent, pent.size()); A(d.pbus, pbus.size()); A(d.pinst, pinst.size());
-  A(d.big, big.size());
+  A(d.big, big.size()); A(d.task_off, K + 1); A(d.big_off, K + 1);
   d.E = (int)E;
   d.NT = (int)(pbus.size() / 32);
   d.NBIG = (int)(big.size() / 2);
@@ -463,6 +477,8 @@ acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_o
   U(d.pd, pd); U(d.qd, qd); U(d.gs, gs); U(d.bs, bs); U(d.wmin, wmin); U(d.wmax, wmax); U(d.isref, isref);
   U(d.end_ptr, end_ptr); U(d.end_idx, end_idx); U(d.gen_ptr, gen_ptr);
   U(d.ent, ent); U(d.ebus, ebus); U(d.pent, pent); U(d.pbus, pbus); U(d.pinst, pinst); U(d.big, big);
+  U(d.task_off, task_off); U(d.big_off, big_off);
+  c->h_task_off = task_off;
   U(d.f, f); U(d.t, t); U(d.s2, s2); U(d.angmin, amin); U(d.angmax, amax);
   U(d.gbus, gbus);
   std::vector<double> v_pmin = P(pmin), v_pmax = P(pmax), v_qmin = P(qmin), v_qmax = P(qmax), v_cq = P(cq),
@@ -625,7 +641,7 @@ acopf_status acopf_tune(acopf_handle h, int32_t block_threads, int32_t ctas_per_
   }
   if (ctas_per_sm >= 0) c->ctas_per_sm = ctas_per_sm;
   if (sweep_stages >= 0) {
-    if (sweep_stages > 3) return fail(c, ACOPF_EINVAL, "acopf_tune: sweep_stages must be 0, 1, 2 or 3");
+    if (sweep_stages > 4) return fail(c, ACOPF_EINVAL, "acopf_tune: sweep_stages must be 0, 1, 2, 3 or 4");
     c->sweep_stages = sweep_stages;
   }
   drop_graph(c);  // the launch shape is baked into a captured graph
@@ -914,7 +930,7 @@ static std::string tune_key(Ctx* c) {
     return k;
   };
   char buf[128];
-  snprintf(buf, sizeof(buf), "v2-sm%d-%s-K%d-B%d-L%d", c->num_sms, c->precision == ACOPF_MIXED ? "mixed" : "fp64",
+  snprintf(buf, sizeof(buf), "v3-sm%d-%s-K%d-B%d-L%d", c->num_sms, c->precision == ACOPF_MIXED ? "mixed" : "fp64",
            lg(c->d.K), lg(c->d.B), lg(c->d.L));
   return buf;
 }
@@ -944,7 +960,7 @@ static bool cache_lookup(const char* path, const std::string& key, int shape[3])
     if (sscanf(p, "\"block_threads\": %d", &bt) != 1 || sscanf(q, "\"ctas_per_sm\": %d", &cps) != 1 ||
         sscanf(r, "\"stages\": %d", &st) != 1)
       continue;
-    if (bt < 32 || bt > 256 || bt % 32 || cps < 0 || st < 0 || st > 3) continue;
+    if (bt < 32 || bt > 256 || bt % 32 || cps < 0 || st < 0 || st > 4) continue;
     shape[0] = bt; shape[1] = cps; shape[2] = st;
     return true;
   }
@@ -997,10 +1013,11 @@ acopf_status acopf_autotune(acopf_handle h, const char* cache_path, int32_t iter
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     const int threads[3] = {64, 128, 256};
-    // record access: in place (0), staged tiles (1, 2; FP32 sweep only), held in registers (3)
-    const int modes_mixed[4] = {0, 1, 2, 3}, modes_fp64[2] = {0, 3};
+    // record access: in place (0), staged tiles (1, 2; FP32 sweep only), held
+    // in registers (3); one thread-block cluster per instance (4)
+    const int modes_mixed[5] = {0, 1, 2, 3, 4}, modes_fp64[3] = {0, 3, 4};
     const int* modes = c->precision == ACOPF_MIXED ? modes_mixed : modes_fp64;
-    const int nmodes = c->precision == ACOPF_MIXED ? 4 : 2;
+    const int nmodes = c->precision == ACOPF_MIXED ? 5 : 3;
     for (int ti = 0; ti < 3; ++ti)
       for (int cps = 0; cps <= 1; ++cps)
         for (int mi = 0; mi < nmodes; ++mi) {

@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/acopf.h"
 
@@ -93,6 +94,9 @@ struct Dev {
   int *pent, *pbus, *pinst;
   int* big;
   int E, NT, NBIG;
+  // first warp task and first big task of every instance (K + 1 each); no
+  // task holds buses of two instances
+  int *task_off, *big_off;
   // branches
   int *f, *t;
   double* Y;        // [8][L]: gii bii gij bij gji bji gjj bjj
@@ -186,7 +190,11 @@ struct Ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double prof_ms = 0.0;
   int64_t prof_sweeps = 0, prof_iters = 0;
-  int sweep_stages = 0;  // FP32 sweep: branch-tile buffers per CTA (0: records read in place)
+  int sweep_stages = 0;  // record access of the sweep (acopf_tune), 4: one thread-block cluster per instance
+  int cluster_cs = 1;         // cluster size of sweep_stages 4, chosen for
+  int cluster_threads = -1;   // this CTA size (-1: not chosen yet)
+  bool cluster_res = false;   // and whether every component of an instance has a thread (static data in registers)
+  std::vector<int> h_task_off;  // host copy of d.task_off
   // warm start staged by acopf_set_warm_start / acopf_set_warm_start_device
   bool warm_x = false, warm_lam = false, warm_rho = false;
   int* d_gen_iperm = nullptr;  // device copy of h_gen_iperm (allocated on first use)

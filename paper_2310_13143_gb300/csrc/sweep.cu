@@ -344,10 +344,11 @@ struct ResDst {
   unsigned long long* acc;  // shared [2][K] or null
   unsigned long long* slots;
   int K, slot;
+  int kbase;  // instance of acc[0] (a cluster's one-instance accumulator; 0 otherwise)
   __device__ __forceinline__ void put(int inst, double r, double s) const {
     if (acc) {
-      if (r > 0.0) atomicMax(&acc[inst], (unsigned long long)__double_as_longlong(r));
-      if (s > 0.0) atomicMax(&acc[K + inst], (unsigned long long)__double_as_longlong(s));
+      if (r > 0.0) atomicMax(&acc[inst - kbase], (unsigned long long)__double_as_longlong(r));
+      if (s > 0.0) atomicMax(&acc[K + inst - kbase], (unsigned long long)__double_as_longlong(s));
     } else {
       if (r > 0.0) atomicMax(&slots[(slot * 2 + 0) * K + inst], (unsigned long long)__double_as_longlong(r));
       if (s > 0.0) atomicMax(&slots[(slot * 2 + 1) * K + inst], (unsigned long long)__double_as_longlong(s));
@@ -618,14 +619,14 @@ struct TaskData {
   int isref;
 };
 
-template <typename T>
+template <typename T, bool kDone = true>
 __device__ __forceinline__ TaskData<T> task_load(const Dev& d, const TaskStatic<T>& st, const int* s_done) {
   TaskData<T> a;
   a.s = st.s;
   a.last = st.last;
   a.br = st.br;
   a.isref = st.isref;
-  if (a.s.bus >= 0 && s_done[a.s.inst]) {
+  if (kDone && a.s.bus >= 0 && s_done[a.s.inst]) {
     a.s.bus = a.s.inst = -1;
     a.last = false;
   }
@@ -676,14 +677,14 @@ __device__ __forceinline__ void bus_task_pair(const Dev& d, const TaskData<T>& a
 }
 
 // one bus with more than 32 entries (entries [q0, q1) of ent); lanes loop
-template <typename T>
+template <typename T, bool kDone = true>
 __device__ void bus_task_big(const SweepP<T>& p, int q0, int q1, const ResDst& dst, const int* s_done) {
   const Dev& d = p.d;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int bus = d.ebus[q0];
   const int inst = d.bus_inst[bus];
-  if (s_done[inst]) {
+  if (kDone && s_done[inst]) {
     res_max2(dst, T(0), T(0), -1);
     return;
   }
@@ -870,7 +871,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && !RES) ? 2 : 1) k_sweep
     if (prof) { tp1 = gtimer(); atomicAdd(&d.phase_ns[0], tp1 - tp0); }
     if (!grid_barrier(d.bar, epoch, d.err, p.spin_limit)) { aborted = true; break; }
     if (prof) { tp0 = gtimer(); atomicAdd(&d.phase_ns[1], tp0 - tp1); }
-    const ResDst dst = {s_acc, d.res_slots, K, slot};
+    const ResDst dst = {s_acc, d.res_slots, K, slot, 0};
     // phase B: buses, in warp tasks of consecutive whole buses, two tasks at a
     // time (every entry belongs to one task, so the loads ahead never read
     // what the current tasks write); loop bounds are uniform per warp so that
@@ -943,6 +944,162 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && !RES) ? 2 : 1) k_sweep
       d.admm_rs[K + k] = __longlong_as_double((long long)d.res_slots[(last * 2 + 1) * K + k]);
     }
   }
+}
+
+// ------------------------------------------------ one cluster per instance
+// With sweep_stages 4 every instance is swept by one thread-block cluster of
+// its own (up to 16 CTAs): the two barriers of an iteration are the cluster's
+// hardware barrier instead of a device-wide one, the residual maxima are
+// accumulated in each CTA's shared memory and combined through distributed
+// shared memory, and clusters of different instances never wait on one
+// another.  There is no spin-wait in this form.
+__device__ __forceinline__ unsigned cluster_ctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_nctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_index() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+// every thread of every CTA of the cluster; memory accesses before it are
+// visible to the whole cluster after it
+__device__ __forceinline__ void cluster_barrier() {
+  __syncwarp();  // the .aligned forms want the whole warp converged
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// the 64-bit word at p's offset in the shared memory of the cluster's CTA `rank`
+__device__ __forceinline__ unsigned long long ld_cluster_u64(const void* p, unsigned rank) {
+  unsigned a;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_addr(p)), "r"(rank));
+  unsigned long long v;
+  asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+  return v;
+}
+
+// RES: the cluster has a thread for every generator and branch of its
+// instance and a warp for every two of its bus tasks (checked by the
+// launcher); the records, instance data and task slots are then loaded once
+// and held in registers, as in the resident form of k_sweep.
+template <typename T, bool RES>
+__global__ void __launch_bounds__(256, 1) k_sweep_cluster(SweepP<T> p) {
+  const Dev& d = p.d;
+  const unsigned FULL = 0xffffffffu;
+  const int K = d.K;
+  const int k = (int)cluster_index();
+  const int cs = (int)cluster_nctarank(), rank = (int)cluster_ctarank();
+  __shared__ unsigned long long s_res[2][2];  // this CTA's maxima (r, s), by iteration parity
+  __shared__ double s_rs[2];
+  __shared__ int s_stop;
+  if (threadIdx.x < 4) (&s_res[0][0])[threadIdx.x] = 0ull;
+  if (d.admm_done[k]) return;  // the whole cluster skips an instance that is not running
+  cluster_barrier();  // every CTA has started before any distributed shared memory access
+  const int nth = cs * blockDim.x, ct = rank * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, cw = ct >> 5, nwc = nth >> 5;
+  const int g0 = d.gen_off[k], nG = d.gen_off[k + 1] - g0, l0 = d.br_off[k], l1 = d.br_off[k + 1];
+  const int t0 = d.task_off[k], t1 = d.task_off[k + 1], b0 = d.big_off[k], b1 = d.big_off[k + 1];
+  const Slot none = {-1, 0, -1};
+  const bool prof = p.profile && blockIdx.x == 0 && threadIdx.x == 0;
+  // RES: this thread's generator or branch record, this warp's two tasks
+  V4<T> rr[kRecChunks];
+  T my_rho = T(0);
+  TaskStatic<T> ta, tb;
+  if (RES) {
+    if (ct < nG) {
+      rr[0] = ((const V4<T>*)d.grec)[g0 + ct];
+      rr[1] = ((const V4<T>*)d.grec)[d.G + g0 + ct];
+    } else if (l0 + ct - nG < l1) {
+      const int l = l0 + ct - nG;
+#pragma unroll
+      for (int c = 0; c < kRecChunks; ++c) rr[c] = ((const V4<T>*)d.lrec)[(size_t)c * d.L + l];
+      my_rho = ((const T*)d.trho_l)[l];
+    }
+    ta = task_static<T>(d, t0 + cw < t1 ? load_slot(d, t0 + cw, lane) : none);
+    tb = task_static<T>(d, t0 + cw + nwc < t1 ? load_slot(d, t0 + cw + nwc, lane) : none);
+  }
+  unsigned long long tp0 = 0, tp1 = 0;
+  int it = 0;
+  bool conv = false;
+  for (it = 0; it < p.max_iter; ++it) {
+    const int slot = it & 1;
+    if (prof) tp0 = gtimer();
+    // this parity's maxima were last read before the first barrier of the previous iteration
+    if (threadIdx.x < 2) s_res[slot][threadIdx.x] = 0ull;
+    // phase A: the instance's generators, then its branches
+    if (RES) {
+      if (ct < nG) {
+        gen_compute(d, g0 + ct, rr[0], rr[1]);
+      } else if (l0 + ct - nG < l1) {
+        const int l = l0 + ct - nG;
+        const V4<T>* Z = (const V4<T>*)d.Z;
+        const V4<T>* LM = (const V4<T>*)d.LAM;
+        line_compute(p, l, RRec<T>{rr}, Z[2 * l], Z[2 * l + 1], LM[2 * l], LM[2 * l + 1], ((const V4<T>*)d.U)[l],
+                     my_rho);
+      }
+    } else {
+      int u = ct;
+      for (; u < nG; u += nth) gen_phase(p, g0 + u, 1.0f);
+      for (int l = l0 + u - nG; l < l1; l += nth) line_phase(p, l, 1.0f);
+    }
+    if (prof) { tp1 = gtimer(); atomicAdd(&d.phase_ns[0], tp1 - tp0); }
+    cluster_barrier();
+    if (prof) { tp0 = gtimer(); atomicAdd(&d.phase_ns[1], tp0 - tp1); }
+    // phase B: the instance's bus tasks, two at a time per warp (warp-uniform loops)
+    const ResDst dst = {&s_res[slot][0], nullptr, 1, slot, k};
+    if (RES) {
+      bus_task_pair(d, task_load<T, false>(d, ta, nullptr), task_load<T, false>(d, tb, nullptr), dst);
+    } else {
+      for (int t = t0 + cw; t < t1; t += 2 * nwc) {
+        const Slot sa = load_slot(d, t, lane);
+        const Slot sb = t + nwc < t1 ? load_slot(d, t + nwc, lane) : none;
+        bus_task_pair(d, task_load<T, false>(d, task_static<T>(d, sa), nullptr),
+                      task_load<T, false>(d, task_static<T>(d, sb), nullptr), dst);
+      }
+    }
+    for (int b = b0 + cw; b < b1; b += nwc) bus_task_big<T, false>(p, d.big[2 * b], d.big[2 * b + 1], dst, nullptr);
+    if (prof) { tp1 = gtimer(); atomicAdd(&d.phase_ns[2], tp1 - tp0); }
+    cluster_barrier();
+    // residual test (Sec. IV-B) on the maxima of all the cluster's CTAs, taken alike by every CTA
+    if (threadIdx.x < 32) {
+      unsigned long long rm = 0ull, sm = 0ull;
+      if (lane < cs) {
+        rm = ld_cluster_u64(&s_res[slot][0], lane);
+        sm = ld_cluster_u64(&s_res[slot][1], lane);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long r2 = __shfl_xor_sync(FULL, rm, o), s2 = __shfl_xor_sync(FULL, sm, o);
+        rm = r2 > rm ? r2 : rm;
+        sm = s2 > sm ? s2 : sm;
+      }
+      if (lane == 0) {
+        const double r = __longlong_as_double((long long)rm), s = __longlong_as_double((long long)sm);
+        s_rs[0] = r;
+        s_rs[1] = s;
+        s_stop = !p.fixed && r <= p.eps && s <= p.eps_dual;
+      }
+    }
+    __syncthreads();
+    if (prof) atomicAdd(&d.phase_ns[3], gtimer() - tp1);
+    if (s_stop) {
+      conv = true;
+      ++it;
+      break;
+    }
+  }
+  if (rank == 0 && threadIdx.x == 0) {
+    if (conv) d.admm_done[k] = 1;
+    d.admm_iters[k] = it;
+    d.admm_rs[k] = it > 0 ? s_rs[0] : 0.0;
+    d.admm_rs[K + k] = it > 0 ? s_rs[1] : 0.0;
+  }
+  cluster_barrier();  // no CTA leaves while another may still read its shared memory
 }
 
 // ADMM state reset: d = 0, z = 0 (and lambda = 0 unless kept); instances that
@@ -1065,6 +1222,90 @@ static acopf_status sweep_shape(Ctx& c, const SweepP<T>& p, SweepShape& sh) {
   return ACOPF_OK;
 }
 
+// Cluster size of sweep_stages 4: enough CTAs for one thread per generator or
+// branch of the largest instance, at most 16, fewer when a cluster of that
+// size cannot be resident.
+template <typename T>
+static int cluster_size(Ctx& c, int threads, cudaLaunchConfig_t& cfg, cudaLaunchAttribute& attr, bool& res) {
+  long items = 1, tasks = 0;
+  for (int k = 0; k < c.d.K; ++k) {
+    long n = (long)(c.h_gen_off[k + 1] - c.h_gen_off[k]) + (c.h_br_off[k + 1] - c.h_br_off[k]);
+    items = n > items ? n : items;
+  }
+  const std::vector<int>& toff = c.h_task_off;
+  for (int k = 0; k < c.d.K; ++k) tasks = toff[k + 1] - toff[k] > tasks ? toff[k + 1] - toff[k] : tasks;
+  int cs = (int)((items + threads - 1) / threads);
+  const long wpb = threads / 32;
+  const int cs_b = (int)((tasks + 2 * wpb - 1) / (2 * wpb));
+  if (cs_b > cs) cs = cs_b;
+  if (cs < 1) cs = 1;
+  res = cs <= 16;
+  if (cs > 16) cs = 16;
+  void* fn = res ? (void*)k_sweep_cluster<T, true> : (void*)k_sweep_cluster<T, false>;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  for (; cs > 1; --cs) {
+    cfg.gridDim = dim3(cs);
+    attr.val.clusterDim.x = cs;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n >= 1) break;
+    cudaGetLastError();
+    res = false;  // a smaller cluster no longer covers every component
+    fn = (void*)k_sweep_cluster<T, false>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  }
+  if (res && (long)cs * threads < items) res = false;
+  return cs;
+}
+
+template <typename T>
+static acopf_status run_sweep_cluster(Ctx& c, const SweepP<T>& p) {
+  const int threads = c.block_threads;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = c.stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (c.cluster_threads != threads) {
+    bool res = false;
+    c.cluster_cs = cluster_size<T>(c, threads, cfg, attr[0], res);
+    c.cluster_res = res;
+    c.cluster_threads = threads;
+  }
+  const int cs = c.cluster_cs;
+  attr[0].val.clusterDim.x = cs;
+  if (!c.capturing) cudaMemsetAsync(c.d.err, 0, sizeof(int), c.stream);
+  cfg.gridDim = dim3((unsigned)(c.d.K * cs));
+  const bool prof = c.profiling && !c.capturing;
+  if (prof) cudaEventRecord(c.ev0, c.stream);
+  cudaError_t e = c.cluster_res ? cudaLaunchKernelEx(&cfg, k_sweep_cluster<T, true>, p)
+                                 : cudaLaunchKernelEx(&cfg, k_sweep_cluster<T, false>, p);
+  c.launches++;
+  if (e != cudaSuccess) {
+    c.last_error = std::string("sweep launch (clusters): ") + cudaGetErrorString(e);
+    return ACOPF_ECUDA;
+  }
+  if (prof) {
+    cudaEventRecord(c.ev1, c.stream);
+    cudaEventSynchronize(c.ev1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c.ev0, c.ev1);
+    c.prof_ms += ms;
+    c.prof_sweeps += 1;
+    int mx = 0;
+    std::vector<int> it(c.d.K);
+    cudaMemcpy(it.data(), c.d.admm_iters, sizeof(int) * c.d.K, cudaMemcpyDeviceToHost);
+    for (int k = 0; k < c.d.K; ++k) mx = it[k] > mx ? it[k] : mx;
+    c.prof_iters += mx;
+  }
+  return ACOPF_OK;
+}
+
 template <typename T>
 static acopf_status run_sweep(Ctx& c, const admm_options& o, int fixed_iters) {
   Dev& d = c.d;
@@ -1082,11 +1323,12 @@ static acopf_status run_sweep(Ctx& c, const admm_options& o, int fixed_iters) {
   p.rb_period = o.rb_period;
   p.rb_mu = o.rb_mu;
   p.rb_tau = o.rb_tau;
-  p.stages = c.sweep_stages == 3 ? 0 : c.sweep_stages;
+  p.stages = c.sweep_stages >= 3 ? 0 : c.sweep_stages;
   p.profile = c.profiling ? 1 : 0;
   p.smem_res = d.K <= kSmemResMax;
   p.line_exact = o.line_solver == 0;
   const int threads = c.block_threads;
+  if (c.sweep_stages == 4 && p.rb_period == 0) return run_sweep_cluster(c, p);
   SweepShape sh;
   acopf_status st = sweep_shape(c, p, sh);
   if (st) return st;
@@ -1204,7 +1446,7 @@ acopf_status run_sweep_static(Ctx& c, const admm_options& o, int n, double* rs, 
   p.rb_period = o.rb_period;
   p.rb_mu = o.rb_mu;
   p.rb_tau = o.rb_tau;
-  p.stages = c.sweep_stages == 3 ? 0 : c.sweep_stages;
+  p.stages = c.sweep_stages >= 3 ? 0 : c.sweep_stages;
   p.profile = 0;  // not timed: acopf_profile covers the handle's own sweeps only
   p.smem_res = d.K <= kSmemResMax;
   p.line_exact = o.line_solver == 0;

@@ -297,7 +297,7 @@ def test_autotune_applies_and_caches_a_shape(tmp_path):
     grids = [gg.grid_30bus()] * 4
     s = binding.Solver(grids, precision="mixed")
     shape, us = s.autotune(cache, iters=20)
-    assert shape[0] in (64, 128, 256) and shape[1] in (0, 1) and shape[2] in (0, 1, 2, 3) and us > 0
+    assert shape[0] in (64, 128, 256) and shape[1] in (0, 1) and shape[2] in (0, 1, 2, 3, 4) and us > 0
     import json
     entries = json.load(open(cache))
     assert len(entries) == 1 and entries[0]["block_threads"] == shape[0]
@@ -314,12 +314,13 @@ def test_mixed_sweep_launch_shapes_agree():
     buffers) or in place from global memory, with any CTA size: the same
     arithmetic on the same values, so the state after a fixed number of
     iterations must be identical.  The resident form (records held in
-    registers) is a separately compiled kernel in which the compiler may
-    contract multiply-adds differently: it must agree to 1e-4 of each
-    array's scale (FP32 rounding carried over 25 iterations)."""
+    registers) and the cluster-per-instance form are separately compiled
+    kernels in which the compiler may contract multiply-adds differently:
+    they must agree to 1e-4 of each array's scale (FP32 rounding carried
+    over 25 iterations)."""
     grids = [gg.geometric_grid(118, seed=7), gg.grid_30bus(), gg.hub_grid(40)]
     ref = None
-    for bt, st in [(256, 1), (256, 0), (128, 2), (64, 0), (96, 1), (256, 3), (64, 3), (32, 3)]:
+    for bt, st in [(256, 1), (256, 0), (128, 2), (64, 0), (96, 1), (256, 3), (64, 3), (32, 3), (256, 4), (64, 4)]:
         s = binding.Solver(grids, precision="mixed")
         s.tune(bt, 0, st)
         s.build_qp(1.0, 2e4, True)
@@ -331,7 +332,7 @@ def test_mixed_sweep_launch_shapes_agree():
             continue
         for a, b in zip(ref, got):
             for key in ("x", "z", "lam", "xg", "zg", "lg", "zb", "nu", "ul"):
-                if st == 3:
+                if st >= 3:
                     # a kernel of its own: the compiler may fuse multiply-adds differently there
                     np.testing.assert_allclose(a[key], b[key], rtol=0, atol=1e-4 * max(1.0, np.abs(a[key]).max()),
                                                err_msg=f"{bt}:{st}:{key}")
@@ -366,12 +367,12 @@ def test_linear_projection_matches_oracle(name):
 
 
 def test_fp64_sweep_resident_records_agree():
-    """The FP64 sweep with records held in registers gives the same state as
-    with records read in place, to the rounding of a separately compiled
-    kernel (1e-9 of each array's scale)."""
+    """The FP64 sweep with records held in registers, or with one cluster per
+    instance, gives the same state as with records read in place, to the
+    rounding of a separately compiled kernel (1e-9 of each array's scale)."""
     grids = [gg.geometric_grid(118, seed=7), gg.grid_30bus(), gg.hub_grid(40)]
     ref = None
-    for bt, st in [(256, 0), (256, 3), (64, 3)]:
+    for bt, st in [(256, 0), (256, 3), (64, 3), (256, 4)]:
         s = binding.Solver(grids, precision="fp64")
         s.tune(bt, 0, st)
         s.build_qp(1.0, 2e4, True)
@@ -383,8 +384,33 @@ def test_fp64_sweep_resident_records_agree():
             continue
         for a, b in zip(ref, got):
             for key in a:
-                if st == 3:
+                if st >= 3:
                     np.testing.assert_allclose(a[key], b[key], rtol=0, atol=1e-9 * max(1.0, np.abs(a[key]).max()),
                                                err_msg=f"{key} threads {bt} mode {st}")
                 else:
                     np.testing.assert_array_equal(a[key], b[key], err_msg=f"{key} threads {bt} mode {st}")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cluster_sweep_solves_like_the_device_wide_sweep(prec):
+    """Sweep mode 4 (one thread-block cluster per instance, hardware cluster
+    barriers, residual maxima combined in distributed shared memory) against
+    the device-wide sweep: full SQP solves of a batch whose instances stop
+    their QPs at different ADMM iterations, including a 2,000-bus grid that
+    spreads over a 16-CTA cluster with several branches per thread."""
+    grids = [gg.grid_30bus(), gg.two_bus(), gg.geometric_grid(118, seed=11), gg.hub_grid(40),
+             gg.grid_2000bus()]
+    opts = binding.default_sqp(tol=1e-4, max_sqp=8, admm=dict(rho=2e4, max_iter=600, eps=1e-4,
+                                                              eps_dual=5e-3 if prec == "mixed" else 0.0))
+    out = []
+    for bt, st in ((256, 0), (128, 4)):
+        s = binding.Solver(grids, precision=prec)
+        s.tune(bt, 0, st)
+        s.sqp_solve_graph(opts, check_every=2)
+        out.append([(s.get_residuals(k), s.get_solution(k)["obj"]) for k in range(len(grids))])
+        s.close()
+    for (ra, oa), (rb, ob) in zip(*out):
+        assert ra["result"] == rb["result"], (ra, rb)
+        np.testing.assert_allclose(ob, oa, rtol=1e-9 if prec == "fp64" else 1e-6)
+        if prec == "fp64":
+            assert ra["sqp_iter"] == rb["sqp_iter"]
