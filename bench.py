@@ -281,8 +281,8 @@ def run_gpu(args, rank, world, local_rank):
     prof = m["prof"]
     avg_ms = prof["sweep_ms"] / max(prof["sweeps"], 1)
     iters_per_launch = prof["admm_iters"] / max(prof["sweeps"], 1)
-    kernel = "k_sweep<float>" if args.precision == "mixed" else "k_sweep<double>"
-    traffic = measured_traffic("syn2000", iters_per_launch) if args.precision == "mixed" and world == 1 else None
+    kernel = sweep_kernel(args.precision, m["launch_shape"]["stages"])
+    traffic = measured_traffic("syn2000", iters_per_launch, kernel) if args.precision == "mixed" and world == 1 else None
     last = m["last"]
     out = {
         "metric": METRIC,
@@ -331,7 +331,8 @@ def run_gpu(args, rank, world, local_rank):
     if world == 1 and not args.no_small:
         sm = small_30bus()
         out["small_30bus"] = sm
-        summary["small_30bus"] = {"solves_s": round(sm["value"], 1), "oracle_solves_s": round(sm["oracle"]["value"], 1)}
+        summary["small_30bus"] = {"solves_s": round(sm["value"], 2), "oracle_solves_s": round(sm["oracle"]["value"], 2),
+                                  "batched_1024_solves_s": round(sm["batched_1024"]["value"], 1)}
     if world == 1 and not args.no_rho_sweep:
         out["rho_sweep"] = rho_sweep(grid, args.precision)
         summary["rho_sweep_solves_s"] = {f"{r['rho']:g}": round(r["solves_per_s"], 2) for r in out["rho_sweep"]}
@@ -401,8 +402,10 @@ def small_30bus(reps=20):
     g = gridgen.grid_30bus()
     opts = binding.default_sqp(tol=1e-4, max_sqp=30)
     stream = torch.cuda.Stream()
+    cache = os.path.join(tempfile.gettempdir(), "acopf_tune_cache.json")
     s = binding.Solver(g, precision="fp64")
     s.set_stream(stream.cuda_stream)
+    shape, _ = s.autotune(cache, iters=30)
     s.sqp_solve(opts)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     conv = 0
@@ -416,6 +419,19 @@ def small_30bus(reps=20):
     t = a.elapsed_time(b) / 1e3
     obj = s.get_solution(0)["obj"]
     s.close()
+    # the same grid under 1,024 correlated load scenarios, one handle, FP64
+    scen = gridgen.scenarios_cholesky(g, 1024, seed=1007)
+    sb = binding.Solver(scen, precision="fp64")
+    sb.set_stream(stream.cuda_stream)
+    bshape, _ = sb.autotune(cache, iters=30)
+    sb.sqp_solve_graph(opts, check_every=2)
+    a.record(stream)
+    sb.sqp_solve_graph(opts, check_every=2)
+    b.record(stream)
+    torch.cuda.synchronize()
+    tb = a.elapsed_time(b) / 1e3
+    bconv = sum(int(_converged(sb.get_residuals(k))) for k in range(len(scen)))
+    sb.close()
     oracle.build()
     m = oracle.Model(g)
     t0 = time.perf_counter()
@@ -429,6 +445,10 @@ def small_30bus(reps=20):
             "value": conv / t, "unit": "solves/s", "ms_per_solve": 1e3 * t / reps, "converged": conv, "of": reps,
             "sqp_iters": r["sqp_iter"], "admm_iters": r["admm_iter"], "objective": obj,
             "objective_rel_diff_vs_oracle": abs(obj - ro["obj"]) / abs(ro["obj"]),
+            "launch_shape": list(shape),
+            "batched_1024": {"value": bconv / tb, "unit": "solves/s", "converged": bconv, "of": len(scen),
+                             "seconds": tb, "launch_shape": list(bshape),
+                             "workload": "1,024 correlated load scenarios of the 30-bus grid in one handle, FP64"},
             "oracle": {"value": oconv / to, "unit": "solves/s", "cores": 1, "solves": n}}
 
 
@@ -795,7 +815,14 @@ def workload_grids(name):
     raise ValueError(name)
 
 
-def measured_traffic(workload, iters_per_launch):
+def sweep_kernel(precision, stages):
+    """Name of the sweep kernel a launch shape runs (sweep_stages 4: one
+    thread-block cluster per instance)."""
+    t = "float" if precision == "mixed" else "double"
+    return f"k_sweep_cluster<{t}>" if stages == 4 else f"k_sweep<{t}>"
+
+
+def measured_traffic(workload, iters_per_launch, kernel=None):
     """DRAM bytes per launch of the FP32 sweep on a workload, from the ncu
     record in profiles/k_sweep_traffic.json, scaled by iterations per launch;
     None when no record exists or the sweep's sources changed since."""
@@ -804,6 +831,8 @@ def measured_traffic(workload, iters_per_launch):
     try:
         with open(os.path.join(HERE, "profiles", "k_sweep_traffic.json")) as f:
             rec = json.load(f)["records"][workload]
+        if kernel is not None and rec["kernel"] != kernel:
+            return None
         h = hashlib.sha256()
         for src in rec["sources"]:
             with open(os.path.join(HERE, src), "rb") as f:
@@ -844,8 +873,8 @@ def sweep_only(grids, precision, iters, launches, warmup, workload=None):
     L = sum(g.nbranch for g in grids)
     G = sum(g.ngen for g in grids)
     us = 1e3 * p["sweep_ms"] / (iters * launches)
-    kernel = "k_sweep<float>" if precision == "mixed" else "k_sweep<double>"
-    traffic = measured_traffic(workload, iters) if precision == "mixed" and workload else None
+    kernel = sweep_kernel(precision, shape[2])
+    traffic = measured_traffic(workload, iters, kernel) if precision == "mixed" and workload else None
     rl = roofline(B, L, G, 4 if precision == "mixed" else 8, iters, us * iters / 1e3, traffic, kernel)
     return {"instances": len(grids), "buses": B, "branches": L, "generators": G, "precision": precision,
             "us_per_iter": us, "admm_iter_per_s": 1e6 / us, "instance_iters_per_s": len(grids) * 1e6 / us,
@@ -864,6 +893,11 @@ def oracle_options():
 
 def _oracle_converged(r):
     return r["status"] == 0 and r["primal"] <= 1e-4 and r["dual"] <= 1e-4
+
+
+def _converged(r, tol=1e-4):
+    """A GPU solve that ended converged with primal and dual infeasibility within tol."""
+    return r["result_name"] == "converged" and r["primal"] <= tol and r["dual"] <= tol
 
 
 def cpu_baseline(grid, min_seconds=10.0):
