@@ -467,6 +467,7 @@ def rho_sweep(grid, precision, rhos=(2e3, 5e3, 1e4, 2e4, 5e4), reps=3):
                                                                    eps_dual=5e-3 if precision == "mixed" else 0.0))
         s = binding.Solver(grid, precision=precision)
         s.set_stream(stream.cuda_stream)
+        s.autotune(os.path.join(tempfile.gettempdir(), "acopf_tune_cache.json"), iters=30)
         s.sqp_solve(opts)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         conv = 0
