@@ -479,6 +479,7 @@ acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_o
   U(d.ent, ent); U(d.ebus, ebus); U(d.pent, pent); U(d.pbus, pbus); U(d.pinst, pinst); U(d.big, big);
   U(d.task_off, task_off); U(d.big_off, big_off);
   c->h_task_off = task_off;
+  c->h_big_off = big_off;
   U(d.f, f); U(d.t, t); U(d.s2, s2); U(d.angmin, amin); U(d.angmax, amax);
   U(d.gbus, gbus);
   std::vector<double> v_pmin = P(pmin), v_pmax = P(pmax), v_qmin = P(qmin), v_qmax = P(qmax), v_cq = P(cq),

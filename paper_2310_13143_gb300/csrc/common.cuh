@@ -194,7 +194,8 @@ struct Ctx {
   int cluster_cs = 1;         // cluster size of sweep_stages 4, chosen for
   int cluster_threads = -1;   // this CTA size (-1: not chosen yet)
   bool cluster_res = false;   // and whether every component of an instance has a thread (static data in registers)
-  std::vector<int> h_task_off;  // host copy of d.task_off
+  bool cluster_dsm = false;   // and whether the state it exchanges stays in distributed shared memory
+  std::vector<int> h_task_off, h_big_off;  // host copies of d.task_off, d.big_off
   // warm start staged by acopf_set_warm_start / acopf_set_warm_start_device
   bool warm_x = false, warm_lam = false, warm_rho = false;
   int* d_gen_iperm = nullptr;  // device copy of h_gen_iperm (allocated on first use)

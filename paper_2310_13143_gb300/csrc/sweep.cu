@@ -155,14 +155,17 @@ __device__ __forceinline__ void tile_issue(const Dev& d, int l0, int n, V4<T>* s
 // b = (lq, uq, rho, 0): clamp((rho z - lambda - f') / (f'' + rho)) and
 // clamp((rho z - lambda) / rho)
 template <typename T>
-__device__ __forceinline__ void gen_compute(const Dev& d, int g, const V4<T>& a, const V4<T>& b) {
-  V2<T> z = ((const V2<T>*)d.ZG)[g];
-  V2<T> lam = ((const V2<T>*)d.LG)[g];
-  T rho = b.z;
+__device__ __forceinline__ V2<T> gen_value(const V4<T>& a, const V4<T>& b, V2<T> z, V2<T> lam) {
+  const T rho = b.z;
   V2<T> x;
   x.x = clampv(div_w(rho * z.x - lam.x - a.x, a.y + rho), a.z, a.w);
   x.y = clampv(div_w(rho * z.y - lam.y, rho), b.x, b.y);
-  ((V2<T>*)d.XG)[g] = x;
+  return x;
+}
+
+template <typename T>
+__device__ __forceinline__ void gen_compute(const Dev& d, int g, const V4<T>& a, const V4<T>& b) {
+  ((V2<T>*)d.XG)[g] = gen_value(a, b, ((const V2<T>*)d.ZG)[g], ((const V2<T>*)d.LG)[g]);
 }
 
 template <typename T>
@@ -242,9 +245,26 @@ __device__ __noinline__ T rb_rescale(const Dev& d, int l, float sc, V4<T>* rs, i
 // memory, a shared-memory tile or registers); values are read where they are
 // used rather than copied to registers, to keep the kernel's register count
 // low.  z, lambda, u and rho are passed in.
+template <typename T, typename Rec, typename Out>
+__device__ __forceinline__ void line_compute_to(const SweepP<T>& p, int l, const Rec& rec, V4<T> z0, V4<T> z1,
+                                                V4<T> l0, V4<T> l1, V4<T> uu, T rho, Out out);
+
 template <typename T, typename Rec>
 __device__ __forceinline__ void line_compute(const SweepP<T>& p, int l, const Rec& rec, V4<T> z0, V4<T> z1, V4<T> l0,
                                              V4<T> l1, V4<T> uu, T rho) {
+  line_compute_to(p, l, rec, z0, z1, l0, l1, uu, rho, [&](const V4<T>& o0, const V4<T>& o1, const V4<T>& ou) {
+    V4<T>* X = (V4<T>*)p.d.X;
+    X[2 * l] = o0;
+    X[2 * l + 1] = o1;
+    ((V4<T>*)p.d.U)[l] = ou;
+  });
+}
+
+// the line update of branch l; out(o0, o1, ou) receives the couplings of its
+// two ends and its line-limit multipliers
+template <typename T, typename Rec, typename Out>
+__device__ __forceinline__ void line_compute_to(const SweepP<T>& p, int l, const Rec& rec, V4<T> z0, V4<T> z1,
+                                                V4<T> l0, V4<T> l1, V4<T> uu, T rho, Out out) {
   const Dev& d = p.d;
   // couplings: flows p_ij q_ij p_ji q_ji (F rows 0..3), voltages dbar 0..3
   const T zf[4] = {z0.x, z0.y, z1.x, z1.y}, lf[4] = {l0.x, l0.y, l1.x, l1.y};
@@ -306,14 +326,11 @@ __device__ __forceinline__ void line_compute(const SweepP<T>& p, int l, const Re
     for (int i = 0; i < 4; ++i) s += rec.again(10 + 4 * f + i) * x[i];
     xf[f] = s;
   }
-  V4<T>* X = (V4<T>*)d.X;
   V4<T> o0, o1, ou;
   o0.x = xf[0]; o0.y = xf[1]; o0.z = x[0]; o0.w = x[1];
   o1.x = xf[2]; o1.y = xf[3]; o1.z = x[2]; o1.w = x[3];
   ou.x = u[0]; ou.y = u[1]; ou.z = u[2]; ou.w = u[3];
-  X[2 * l] = o0;
-  X[2 * l + 1] = o1;
-  ((V4<T>*)d.U)[l] = ou;
+  out(o0, o1, ou);
 }
 
 // line update of branch l reading its record from global memory (rs, stride L)
@@ -478,8 +495,7 @@ __device__ __forceinline__ void entry_sums(int c, const V4<T>& x, const V4<T>& l
 // the 2x2 system (A Q^-1 A') nu = A Q^-1 c - b of the bus's power-balance rows
 // with shunts, then d_w and d_theta; writes ZB, NU
 template <typename T>
-__device__ __forceinline__ void bus_solve(const Dev& d, int bus, V4<T> br, int isref, const T* S, T& n1, T& n2,
-                                          T& dw, T& dth) {
+__device__ __forceinline__ void bus_values(V4<T> br, int isref, const T* S, T& n1, T& n2, T& dw, T& dth) {
   const T gsh = br.z, bsh = br.w;
   const T iQw = S[3] > T(0) ? div_w(T(1), S[3]) : T(0);  // a bus without branch ends has no voltage copies
   const T M11 = S[0] + gsh * gsh * iQw;
@@ -492,6 +508,12 @@ __device__ __forceinline__ void bus_solve(const Dev& d, int bus, V4<T> br, int i
   n2 = div_w(M11 * v2 - M12 * v1, det);
   dw = (S[4] + gsh * n1 - bsh * n2) * iQw;
   dth = (isref || !(S[3] > T(0))) ? T(0) : div_w(S[5], S[3]);
+}
+
+template <typename T>
+__device__ __forceinline__ void bus_solve(const Dev& d, int bus, V4<T> br, int isref, const T* S, T& n1, T& n2,
+                                          T& dw, T& dth) {
+  bus_values(br, isref, S, n1, n2, dw, dth);
   V2<T> zb, nu;
   zb.x = dw; zb.y = dth;
   nu.x = n1; nu.y = n2;
@@ -501,22 +523,33 @@ __device__ __forceinline__ void bus_solve(const Dev& d, int bus, V4<T> br, int i
 
 // bus-side value, multiplier update and residuals of one coupling
 template <typename T>
-__device__ __forceinline__ void entry_update(const Dev& d, int c, const V4<T>& x, const V4<T>& lm, const V4<T>& zo, T r,
-                                             T n1, T n2, T dw, T dth, T& rm, T& sm) {
+__device__ __forceinline__ void entry_store(const Dev& d, int c, const V4<T>& zn, const V4<T>& ln) {
   if (c < 0) {
     const int g = -c - 1;
-    V2<T> zn, ln;
+    ((V2<T>*)d.ZG)[g] = V2<T>{zn.x, zn.y};
+    ((V2<T>*)d.LG)[g] = V2<T>{ln.x, ln.y};
+  } else {
+    ((V4<T>*)d.Z)[c] = zn;
+    ((V4<T>*)d.LAM)[c] = ln;
+  }
+}
+
+// new bus-side value zn and multiplier ln of one coupling, with its residuals
+// (generator couplings in the x, y components, z and w zero)
+template <typename T>
+__device__ __forceinline__ void entry_values(int c, const V4<T>& x, const V4<T>& lm, const V4<T>& zo, T r, T n1, T n2,
+                                             T dw, T dth, T& rm, T& sm, V4<T>& zn, V4<T>& ln) {
+  if (c < 0) {
     zn.x = div_w(lm.x + r * x.x - n1, r);
     zn.y = div_w(lm.y + r * x.y - n2, r);
+    zn.z = zn.w = T(0);
     sm = fmax(sm, r * fmax(fabs(zn.x - zo.x), fabs(zn.y - zo.y)));
     const T rx = x.x - zn.x, ry = x.y - zn.y;
     rm = fmax(rm, fmax(fabs(rx), fabs(ry)));
     ln.x = lm.x + r * rx;
     ln.y = lm.y + r * ry;
-    ((V2<T>*)d.ZG)[g] = zn;
-    ((V2<T>*)d.LG)[g] = ln;
+    ln.z = ln.w = T(0);
   } else {
-    V4<T> zn, ln;
     zn.x = div_w(lm.x + r * x.x + n1, r);
     zn.y = div_w(lm.y + r * x.y + n2, r);
     zn.z = dw;
@@ -530,9 +563,15 @@ __device__ __forceinline__ void entry_update(const Dev& d, int c, const V4<T>& x
     ln.y = lm.y + r * ry;
     ln.z = lm.z + r * rw;
     ln.w = lm.w + r * rt;
-    ((V4<T>*)d.Z)[c] = zn;
-    ((V4<T>*)d.LAM)[c] = ln;
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void entry_update(const Dev& d, int c, const V4<T>& x, const V4<T>& lm, const V4<T>& zo, T r,
+                                             T n1, T n2, T dw, T dth, T& rm, T& sm) {
+  V4<T> zn, ln;
+  entry_values(c, x, lm, zo, r, n1, n2, dw, dth, rm, sm, zn, ln);
+  entry_store(d, c, zn, ln);
 }
 
 // segmented inclusive scan of the six sums by bus id: the last lane of each
@@ -1102,6 +1141,268 @@ __global__ void __launch_bounds__(256, 1) k_sweep_cluster(SweepP<T> p) {
   cluster_barrier();  // no CTA leaves while another may still read its shared memory
 }
 
+// ---------------------------------- cluster form with its state in shared memory
+// Distributed shared memory addresses and stores (shared::cluster window).
+__device__ __forceinline__ unsigned cluster_addr(const void* p, unsigned rank) {
+  unsigned a;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_addr(p)), "r"(rank));
+  return a;
+}
+__device__ __forceinline__ void st_cluster(unsigned a, const V4<float>& v) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void st_cluster(unsigned a, const V4<double>& v) {
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v.x), "d"(v.y) : "memory");
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(a + 16), "d"(v.z), "d"(v.w) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(unsigned a, unsigned v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+// One bus-task lane of the shared-memory form: its entry, the coupling's
+// multiplier and old bus-side value (held from one iteration to the next),
+// the penalty, and where its new bus-side value and multiplier go.
+template <typename T>
+struct DsmLane {
+  TaskStatic<T> st;
+  V4<T> lm, zo;
+  T r;
+  unsigned to;  // shared::cluster address of the owner's (z, lambda) pair
+};
+
+// Two tasks of one warp: x from this CTA's receive buffers (xa, xb), the bus
+// update of eq. bus_kernel and the multiplier update of eq. multiplier, and
+// the new (z, lambda) pushed to the generator's or branch's CTA.
+template <typename T>
+__device__ __forceinline__ void bus_pair_dsm(DsmLane<T>& a, DsmLane<T>& b, const V4<T>& xa, const V4<T>& xb,
+                                             const ResDst& dst, V2<T>& zba, V2<T>& nua, V2<T>& zbb, V2<T>& nub) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const bool ea = a.st.s.bus >= 0, eb = b.st.s.bus >= 0;
+  T Sa[6] = {0, 0, 0, 0, 0, 0}, Sb[6] = {0, 0, 0, 0, 0, 0};
+  if (ea) entry_sums(a.st.s.code, xa, a.lm, a.r, Sa);
+  if (eb) entry_sums(b.st.s.code, xb, b.lm, b.r, Sb);
+  seg_scan2(a.st.s.bus, Sa, b.st.s.bus, Sb);
+  T n1a = 0, n2a = 0, dwa = 0, dta = 0, n1b = 0, n2b = 0, dwb = 0, dtb = 0;
+  if (a.st.last) {
+    bus_values(a.st.br, a.st.isref, Sa, n1a, n2a, dwa, dta);
+    zba = V2<T>{dwa, dta};
+    nua = V2<T>{n1a, n2a};
+  }
+  if (b.st.last) {
+    bus_values(b.st.br, b.st.isref, Sb, n1b, n2b, dwb, dtb);
+    zbb = V2<T>{dwb, dtb};
+    nub = V2<T>{n1b, n2b};
+  }
+  const unsigned ha = __ballot_sync(FULL, a.st.last) >> lane, hb = __ballot_sync(FULL, b.st.last) >> lane;
+  const int srca = ha ? lane + __ffs(ha) - 1 : lane, srcb = hb ? lane + __ffs(hb) - 1 : lane;
+  n1a = __shfl_sync(FULL, n1a, srca);
+  n1b = __shfl_sync(FULL, n1b, srcb);
+  n2a = __shfl_sync(FULL, n2a, srca);
+  n2b = __shfl_sync(FULL, n2b, srcb);
+  dwa = __shfl_sync(FULL, dwa, srca);
+  dwb = __shfl_sync(FULL, dwb, srcb);
+  dta = __shfl_sync(FULL, dta, srca);
+  dtb = __shfl_sync(FULL, dtb, srcb);
+  T rma = T(0), sma = T(0), rmb = T(0), smb = T(0);
+  if (ea) {
+    V4<T> zn, ln;
+    entry_values(a.st.s.code, xa, a.lm, a.zo, a.r, n1a, n2a, dwa, dta, rma, sma, zn, ln);
+    st_cluster(a.to, zn);
+    st_cluster(a.to + sizeof(V4<T>), ln);
+    a.zo = zn;
+    a.lm = ln;
+    if (!(rma == rma)) rma = T(1e30);
+    if (!(sma == sma)) sma = T(1e30);
+  }
+  if (eb) {
+    V4<T> zn, ln;
+    entry_values(b.st.s.code, xb, b.lm, b.zo, b.r, n1b, n2b, dwb, dtb, rmb, smb, zn, ln);
+    st_cluster(b.to, zn);
+    st_cluster(b.to + sizeof(V4<T>), ln);
+    b.zo = zn;
+    b.lm = ln;
+    if (!(rmb == rmb)) rmb = T(1e30);
+    if (!(smb == smb)) smb = T(1e30);
+  }
+  res_max2_pair(dst, rma, sma, a.st.s.inst, rmb, smb, b.st.s.inst);
+}
+
+// The resident cluster form with the exchanged state in shared memory: the
+// cluster has a thread for every generator and branch of its instance and a
+// warp for every two of its bus tasks, and the instance has no bus of more
+// than 32 entries (checked by the launcher).  Each generator or branch keeps
+// its coupling pairs (z, lambda) in its own CTA's shared memory, where the
+// bus lanes push them; each bus lane keeps its coupling's x in its CTA's
+// shared memory, where the generator or branch pushes it.  Within the sweep
+// no state goes through global memory: it is read at the start and written
+// back at the end.  Dynamic shared memory: (z, lambda) of both ends of every
+// item [4 blockDim], x of this CTA's lanes for two tasks [2 blockDim], and
+// the lanes' receive addresses per item end [2 blockDim].
+template <typename T>
+__global__ void __launch_bounds__(256, 1) k_sweep_cluster_dsm(SweepP<T> p) {
+  const Dev& d = p.d;
+  const unsigned FULL = 0xffffffffu;
+  const int K = d.K;
+  const int k = (int)cluster_index();
+  const int cs = (int)cluster_nctarank(), rank = (int)cluster_ctarank();
+  __shared__ unsigned long long s_res[2][2];  // this CTA's maxima (r, s), by iteration parity
+  __shared__ double s_rs[2];
+  __shared__ int s_stop;
+  extern __shared__ __align__(16) unsigned char s_dyn_c[];
+  const int bt = blockDim.x;
+  V4<T>* s_zl = (V4<T>*)s_dyn_c;
+  V4<T>* s_xin = s_zl + 4 * bt;
+  unsigned* s_xcons = (unsigned*)(s_xin + 2 * bt);
+  if (threadIdx.x < 4) (&s_res[0][0])[threadIdx.x] = 0ull;
+  if (d.admm_done[k]) return;  // the whole cluster skips an instance that is not running
+  const int nth = cs * bt, ct = rank * bt + threadIdx.x;
+  const int lane = threadIdx.x & 31, cw = ct >> 5, nwc = nth >> 5;
+  const int g0 = d.gen_off[k], nG = d.gen_off[k + 1] - g0, l0 = d.br_off[k], l1 = d.br_off[k + 1];
+  const int t0 = d.task_off[k], t1 = d.task_off[k + 1];
+  const Slot none = {-1, 0, -1};
+  const bool prof = p.profile && blockIdx.x == 0 && threadIdx.x == 0;
+  // this thread's generator or branch, its record, multipliers and (z, lambda)
+  const int j = threadIdx.x;
+  const bool is_gen = ct < nG, is_br = !is_gen && l0 + ct - nG < l1;
+  const int g = g0 + ct, l = l0 + ct - nG;
+  V4<T> rr[kRecChunks];
+  T my_rho = T(0);
+  V4<T> uu = {T(0), T(0), T(0), T(0)};
+  const V4<T> zero4 = {T(0), T(0), T(0), T(0)};
+  if (is_gen) {
+    rr[0] = ((const V4<T>*)d.grec)[g];
+    rr[1] = ((const V4<T>*)d.grec)[d.G + g];
+    const V2<T> z = ((const V2<T>*)d.ZG)[g], lg = ((const V2<T>*)d.LG)[g];
+    s_zl[4 * j] = V4<T>{z.x, z.y, T(0), T(0)};
+    s_zl[4 * j + 1] = V4<T>{lg.x, lg.y, T(0), T(0)};
+  } else if (is_br) {
+#pragma unroll
+    for (int c = 0; c < kRecChunks; ++c) rr[c] = ((const V4<T>*)d.lrec)[(size_t)c * d.L + l];
+    my_rho = ((const T*)d.trho_l)[l];
+    uu = ((const V4<T>*)d.U)[l];
+    s_zl[4 * j] = ((const V4<T>*)d.Z)[2 * l];
+    s_zl[4 * j + 1] = ((const V4<T>*)d.LAM)[2 * l];
+    s_zl[4 * j + 2] = ((const V4<T>*)d.Z)[2 * l + 1];
+    s_zl[4 * j + 3] = ((const V4<T>*)d.LAM)[2 * l + 1];
+  }
+  // this warp's two tasks; every lane with an entry tells the owner of its
+  // coupling where to push x, and keeps where to push (z, lambda)
+  DsmLane<T> A, B;
+  auto lane_init = [&](DsmLane<T>& e, int t, int w) {
+    e.st = task_static<T>(d, t < t1 ? load_slot(d, t, lane) : none);
+    e.lm = e.zo = zero4;
+    e.r = T(1);
+    e.to = 0u;
+    if (e.st.s.bus >= 0) {
+      V4<T> x;
+      entry_load(d, e.st.s.code, x, e.lm, e.zo, e.r);
+      const int c = e.st.s.code;
+      const int uo = c < 0 ? (-c - 1) - g0 : nG + (c >> 1) - l0;
+      const int side = c < 0 ? 0 : (c & 1);
+      const unsigned orank = (unsigned)(uo / bt), oj = (unsigned)(uo % bt);
+      e.to = cluster_addr(&s_zl[4 * oj + 2 * side], orank);
+      st_cluster_u32(cluster_addr(&s_xcons[2 * oj + side], orank), cluster_addr(&s_xin[w * bt + threadIdx.x], rank));
+    }
+  };
+  cluster_barrier();  // every CTA has started before any distributed shared memory access
+  lane_init(A, t0 + cw, 0);
+  lane_init(B, t0 + cw + nwc, 1);
+  cluster_barrier();  // the receive addresses are in place
+  unsigned xc0 = 0u, xc1 = 0u;
+  if (is_gen || is_br) {
+    xc0 = s_xcons[2 * j];
+    xc1 = s_xcons[2 * j + 1];
+  }
+  V4<T> x0 = zero4, x1 = zero4;
+  V2<T> xg = {T(0), T(0)}, zba = {T(0), T(0)}, nua = zba, zbb = zba, nub = zba;
+  unsigned long long tp0 = 0, tp1 = 0;
+  int it = 0;
+  bool conv = false;
+  for (it = 0; it < p.max_iter; ++it) {
+    const int slot = it & 1;
+    if (prof) tp0 = gtimer();
+    if (threadIdx.x < 2) s_res[slot][threadIdx.x] = 0ull;
+    // phase A
+    if (is_gen) {
+      const V4<T> z = s_zl[4 * j], lm = s_zl[4 * j + 1];
+      xg = gen_value(rr[0], rr[1], V2<T>{z.x, z.y}, V2<T>{lm.x, lm.y});
+      st_cluster(xc0, V4<T>{xg.x, xg.y, T(0), T(0)});
+    } else if (is_br) {
+      line_compute_to(p, l, RRec<T>{rr}, s_zl[4 * j], s_zl[4 * j + 2], s_zl[4 * j + 1], s_zl[4 * j + 3], uu, my_rho,
+                      [&](const V4<T>& o0, const V4<T>& o1, const V4<T>& ou) {
+                        st_cluster(xc0, o0);
+                        st_cluster(xc1, o1);
+                        x0 = o0;
+                        x1 = o1;
+                        uu = ou;
+                      });
+    }
+    if (prof) { tp1 = gtimer(); atomicAdd(&d.phase_ns[0], tp1 - tp0); }
+    cluster_barrier();
+    if (prof) { tp0 = gtimer(); atomicAdd(&d.phase_ns[1], tp0 - tp1); }
+    // phase B
+    const ResDst dst = {&s_res[slot][0], nullptr, 1, slot, k};
+    bus_pair_dsm(A, B, s_xin[threadIdx.x], s_xin[bt + threadIdx.x], dst, zba, nua, zbb, nub);
+    if (prof) { tp1 = gtimer(); atomicAdd(&d.phase_ns[2], tp1 - tp0); }
+    cluster_barrier();
+    // residual test (Sec. IV-B) on the maxima of all the cluster's CTAs, taken alike by every CTA
+    if (threadIdx.x < 32) {
+      unsigned long long rm = 0ull, sm = 0ull;
+      if (lane < cs) {
+        rm = ld_cluster_u64(&s_res[slot][0], lane);
+        sm = ld_cluster_u64(&s_res[slot][1], lane);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long r2 = __shfl_xor_sync(FULL, rm, o), s2 = __shfl_xor_sync(FULL, sm, o);
+        rm = r2 > rm ? r2 : rm;
+        sm = s2 > sm ? s2 : sm;
+      }
+      if (lane == 0) {
+        const double r = __longlong_as_double((long long)rm), s = __longlong_as_double((long long)sm);
+        s_rs[0] = r;
+        s_rs[1] = s;
+        s_stop = !p.fixed && r <= p.eps && s <= p.eps_dual;
+      }
+    }
+    __syncthreads();
+    if (prof) atomicAdd(&d.phase_ns[3], gtimer() - tp1);
+    if (s_stop) {
+      conv = true;
+      ++it;
+      break;
+    }
+  }
+  // the state back to global memory
+  if (it > 0) {
+    if (is_gen) ((V2<T>*)d.XG)[g] = xg;
+    if (is_br) {
+      ((V4<T>*)d.X)[2 * l] = x0;
+      ((V4<T>*)d.X)[2 * l + 1] = x1;
+      ((V4<T>*)d.U)[l] = uu;
+    }
+    if (A.st.s.bus >= 0) entry_store(d, A.st.s.code, A.zo, A.lm);
+    if (B.st.s.bus >= 0) entry_store(d, B.st.s.code, B.zo, B.lm);
+    if (A.st.last) {
+      ((V2<T>*)d.ZB)[A.st.s.bus] = zba;
+      ((V2<T>*)d.NU)[A.st.s.bus] = nua;
+    }
+    if (B.st.last) {
+      ((V2<T>*)d.ZB)[B.st.s.bus] = zbb;
+      ((V2<T>*)d.NU)[B.st.s.bus] = nub;
+    }
+  }
+  if (rank == 0 && threadIdx.x == 0) {
+    if (conv) d.admm_done[k] = 1;
+    d.admm_iters[k] = it;
+    d.admm_rs[k] = it > 0 ? s_rs[0] : 0.0;
+    d.admm_rs[K + k] = it > 0 ? s_rs[1] : 0.0;
+  }
+  cluster_barrier();  // no CTA leaves while another may still read its shared memory
+}
+
 // ADMM state reset: d = 0, z = 0 (and lambda = 0 unless kept); instances that
 // are no longer running keep their state
 template <typename T>
@@ -1271,20 +1572,44 @@ static acopf_status run_sweep_cluster(Ctx& c, const SweepP<T>& p) {
   cfg.stream = c.stream;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  const size_t dsm_smem = (size_t)threads * (6 * sizeof(V4<T>) + 2 * sizeof(unsigned));
   if (c.cluster_threads != threads) {
     bool res = false;
     c.cluster_cs = cluster_size<T>(c, threads, cfg, attr[0], res);
     c.cluster_res = res;
     c.cluster_threads = threads;
+    // the shared-memory form: FP32, resident, and no bus of more than 32 entries
+    bool dsm = res && sizeof(T) == 4;
+    for (int k = 0; dsm && k < c.d.K; ++k) dsm = c.h_big_off[k + 1] == c.h_big_off[k];
+    if constexpr (sizeof(T) == 4) if (dsm) {
+      cudaFuncSetAttribute(k_sweep_cluster_dsm<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      cudaFuncSetAttribute(k_sweep_cluster_dsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm_smem);
+      cfg.gridDim = dim3(c.cluster_cs);
+      attr[0].val.clusterDim.x = c.cluster_cs;
+      cfg.dynamicSmemBytes = dsm_smem;
+      int n = 0;
+      dsm = cudaOccupancyMaxActiveClusters(&n, (void*)k_sweep_cluster_dsm<T>, &cfg) == cudaSuccess && n >= 1;
+      cudaGetLastError();
+      cfg.dynamicSmemBytes = 0;
+    }
+    c.cluster_dsm = dsm;
   }
   const int cs = c.cluster_cs;
   attr[0].val.clusterDim.x = cs;
+  if (c.cluster_dsm) cfg.dynamicSmemBytes = dsm_smem;
   if (!c.capturing) cudaMemsetAsync(c.d.err, 0, sizeof(int), c.stream);
   cfg.gridDim = dim3((unsigned)(c.d.K * cs));
   const bool prof = c.profiling && !c.capturing;
   if (prof) cudaEventRecord(c.ev0, c.stream);
-  cudaError_t e = c.cluster_res ? cudaLaunchKernelEx(&cfg, k_sweep_cluster<T, true>, p)
-                                 : cudaLaunchKernelEx(&cfg, k_sweep_cluster<T, false>, p);
+  cudaError_t e;
+  if constexpr (sizeof(T) == 4) {
+    e = c.cluster_dsm   ? cudaLaunchKernelEx(&cfg, k_sweep_cluster_dsm<T>, p)
+        : c.cluster_res ? cudaLaunchKernelEx(&cfg, k_sweep_cluster<T, true>, p)
+                        : cudaLaunchKernelEx(&cfg, k_sweep_cluster<T, false>, p);
+  } else {
+    e = c.cluster_res ? cudaLaunchKernelEx(&cfg, k_sweep_cluster<T, true>, p)
+                      : cudaLaunchKernelEx(&cfg, k_sweep_cluster<T, false>, p);
+  }
   c.launches++;
   if (e != cudaSuccess) {
     c.last_error = std::string("sweep launch (clusters): ") + cudaGetErrorString(e);

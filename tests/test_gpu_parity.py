@@ -414,3 +414,38 @@ def test_cluster_sweep_solves_like_the_device_wide_sweep(prec):
         np.testing.assert_allclose(ob, oa, rtol=1e-9 if prec == "fp64" else 1e-6)
         if prec == "fp64":
             assert ra["sqp_iter"] == rb["sqp_iter"]
+
+
+def test_cluster_sweep_with_state_in_shared_memory():
+    """Grids with no bus of more than 32 couplings, a cluster that covers each
+    of them: the FP32 cluster sweep keeps the state it exchanges (x one way,
+    z and lambda the other) in distributed shared memory and writes it back
+    at the end.  Its state after a fixed number of iterations matches the
+    device-wide sweep to FP32 rounding, and so does a full SQP solve."""
+    grids = [gg.grid_30bus(), gg.two_bus(), gg.geometric_grid(118, seed=11), gg.grid_2000bus()]
+    ref = None
+    for bt, st in ((256, 0), (256, 4), (224, 4)):
+        s = binding.Solver(grids, precision="mixed")
+        s.tune(bt, 0, st)
+        s.build_qp(1.0, 2e4, True)
+        s.admm_iterate(25, binding.default_admm())
+        got = [s.get_admm_state(k) for k in range(len(grids))]
+        s.close()
+        if ref is None:
+            ref = got
+            continue
+        for a, b in zip(ref, got):
+            for key in ("x", "z", "lam", "xg", "zg", "lg", "zb", "nu", "ul"):
+                np.testing.assert_allclose(b[key], a[key], rtol=0, atol=1e-4 * max(1.0, np.abs(a[key]).max()),
+                                           err_msg=f"{bt}:{st}:{key}")
+    opts = binding.default_sqp(tol=1e-4, max_sqp=8, admm=dict(rho=2e4, max_iter=600, eps=1e-4, eps_dual=5e-3))
+    out = []
+    for st in (0, 4):
+        s = binding.Solver(grids, precision="mixed")
+        s.tune(256, 0, st)
+        s.sqp_solve_graph(opts, check_every=2)
+        out.append([(s.get_residuals(k), s.get_solution(k)["obj"]) for k in range(len(grids))])
+        s.close()
+    for (ra, oa), (rb, ob) in zip(*out):
+        assert ra["result"] == rb["result"], (ra, rb)
+        np.testing.assert_allclose(ob, oa, rtol=1e-6)
