@@ -56,8 +56,12 @@ def _gpu_opts(o: oracle.SqpOptions):
                                          warm=o.warm_lambda))
 
 
-@pytest.mark.parametrize("name", list(RUNS))
-def test_sqp_history_matches_oracle(name):
+# the same runs with the sweep in one thread-block cluster per instance (sweep_stages 4)
+CLUSTER_RUNS = ("syn30_A", "syn30_default", "syn2000_bench", "soc_accepted", "restore_and_back")
+
+
+@pytest.mark.parametrize("name,cluster", [(n, False) for n in RUNS] + [(n, True) for n in CLUSTER_RUNS])
+def test_sqp_history_matches_oracle(name, cluster):
     make, run = RUNS[name]
     g = make()
     o = oracle.SqpOptions(**run)
@@ -66,6 +70,8 @@ def test_sqp_history_matches_oracle(name):
     want = alg1(m, o, line_fail)
     np.testing.assert_array_equal(want, m.sqp(o)["hist"])  # the driver is the oracle's own loop
     s = binding.Solver(g, precision="fp64")
+    if cluster:
+        s.tune(256, 0, 4)
     s.sqp_solve(_gpu_opts(o))
     got = s.get_history(0)
     res = s.get_residuals(0)
