@@ -332,6 +332,7 @@ def run_gpu(args, rank, world, local_rank):
         sm = small_30bus()
         out["small_30bus"] = sm
         summary["small_30bus"] = {"solves_s": round(sm["value"], 2), "oracle_solves_s": round(sm["oracle"]["value"], 2),
+                                  "mixed_solves_s": round(sm["mixed"]["value"], 2),
                                   "batched_1024_solves_s": round(sm["batched_1024"]["value"], 1)}
     if world == 1 and not args.no_rho_sweep:
         out["rho_sweep"] = rho_sweep(grid, args.precision)
@@ -393,7 +394,8 @@ def small_30bus(reps=20):
     """The synthetic 30-bus grid (the first workload): plain FP64 solves on the
     GPU, one handle, from the flat start to 1e-4 with the solver's default
     ADMM settings (rho 2e4, eps 1e-4), against the oracle's single-thread
-    solves of the same grid and settings."""
+    solves of the same grid and settings; beside them the mixed-precision
+    path on the same grid and 1,024 load scenarios of it in one FP64 handle."""
     import torch
 
     import oracle
@@ -419,6 +421,24 @@ def small_30bus(reps=20):
     t = a.elapsed_time(b) / 1e3
     obj = s.get_solution(0)["obj"]
     s.close()
+    # the same grid on the mixed-precision path (FP32 sweep, its dual residual
+    # tested against 5e-3: rho times the FP32 resolution of z bounds it below)
+    mopts = binding.default_sqp(tol=1e-4, max_sqp=30, admm=dict(eps_dual=5e-3))
+    sm = binding.Solver(g, precision="mixed")
+    sm.set_stream(stream.cuda_stream)
+    mshape, _ = sm.autotune(cache, iters=30)
+    sm.sqp_solve(mopts)
+    mconv = 0
+    a.record(stream)
+    for _ in range(reps):
+        sm.sqp_solve(mopts)
+        mconv += int(_converged(sm.get_residuals(0)))
+    b.record(stream)
+    torch.cuda.synchronize()
+    tm = a.elapsed_time(b) / 1e3
+    mres = sm.get_residuals(0)
+    mobj = sm.get_solution(0)["obj"]
+    sm.close()
     # the same grid under 1,024 correlated load scenarios, one handle, FP64
     scen = gridgen.scenarios_cholesky(g, 1024, seed=1007)
     sb = binding.Solver(scen, precision="fp64")
@@ -446,6 +466,10 @@ def small_30bus(reps=20):
             "sqp_iters": r["sqp_iter"], "admm_iters": r["admm_iter"], "objective": obj,
             "objective_rel_diff_vs_oracle": abs(obj - ro["obj"]) / abs(ro["obj"]),
             "launch_shape": list(shape),
+            "mixed": {"value": mconv / tm, "unit": "solves/s", "ms_per_solve": 1e3 * tm / reps, "converged": mconv,
+                      "of": reps, "sqp_iters": mres["sqp_iter"], "admm_iters": mres["admm_iter"],
+                      "objective_rel_diff_vs_oracle": abs(mobj - ro["obj"]) / abs(ro["obj"]),
+                      "launch_shape": list(mshape), "eps_dual": 5e-3},
             "batched_1024": {"value": bconv / tb, "unit": "solves/s", "converged": bconv, "of": len(scen),
                              "seconds": tb, "launch_shape": list(bshape),
                              "workload": "1,024 correlated load scenarios of the 30-bus grid in one handle, FP64"},
