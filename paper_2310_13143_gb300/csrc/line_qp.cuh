@@ -100,36 +100,53 @@ struct Eps<float> {
   static constexpr float v = 1.1920928955078125e-07f;
 };
 
-// Solve A p = r, A = h restricted to the free variables (free bit i set) with
-// unit rows and columns for the fixed ones, by Cholesky.  False on breakdown.
+// Cholesky factor of A = h restricted to the free variables (free bit i set),
+// with unit rows and columns for the fixed ones: the strict lower part l and
+// the reciprocals of the diagonal i.  False on breakdown.
 template <typename T>
-ACOPF_HD inline bool chol4_masked(const T h[10], unsigned fr, const T r[4], T p[4]) {
+struct Chol4 {
+  T l10, l20, l30, l21, l31, l32, i00, i11, i22, i33;
+};
+template <typename T>
+ACOPF_HD inline bool chol4_factor(const T h[10], unsigned fr, Chol4<T>& f) {
   const bool f0 = fr & 1u, f1 = (fr >> 1) & 1u, f2 = (fr >> 2) & 1u, f3 = (fr >> 3) & 1u;
   T a00 = f0 ? h[0] : T(1), a11 = f1 ? h[4] : T(1), a22 = f2 ? h[7] : T(1), a33 = f3 ? h[9] : T(1);
   T a01 = f0 && f1 ? h[1] : T(0), a02 = f0 && f2 ? h[2] : T(0), a03 = f0 && f3 ? h[3] : T(0);
   T a12 = f1 && f2 ? h[5] : T(0), a13 = f1 && f3 ? h[6] : T(0), a23 = f2 && f3 ? h[8] : T(0);
   if (!(a00 > T(0))) return false;
-  T i00 = rsqrt_w(a00);
-  T l10 = a01 * i00, l20 = a02 * i00, l30 = a03 * i00;
-  T d1 = a11 - l10 * l10;
+  f.i00 = rsqrt_w(a00);
+  f.l10 = a01 * f.i00; f.l20 = a02 * f.i00; f.l30 = a03 * f.i00;
+  T d1 = a11 - f.l10 * f.l10;
   if (!(d1 > T(0))) return false;
-  T i11 = rsqrt_w(d1);
-  T l21 = (a12 - l20 * l10) * i11, l31 = (a13 - l30 * l10) * i11;
-  T d2 = a22 - l20 * l20 - l21 * l21;
+  f.i11 = rsqrt_w(d1);
+  f.l21 = (a12 - f.l20 * f.l10) * f.i11; f.l31 = (a13 - f.l30 * f.l10) * f.i11;
+  T d2 = a22 - f.l20 * f.l20 - f.l21 * f.l21;
   if (!(d2 > T(0))) return false;
-  T i22 = rsqrt_w(d2);
-  T l32 = (a23 - l30 * l20 - l31 * l21) * i22;
-  T d3 = a33 - l30 * l30 - l31 * l31 - l32 * l32;
+  f.i22 = rsqrt_w(d2);
+  f.l32 = (a23 - f.l30 * f.l20 - f.l31 * f.l21) * f.i22;
+  T d3 = a33 - f.l30 * f.l30 - f.l31 * f.l31 - f.l32 * f.l32;
   if (!(d3 > T(0))) return false;
-  T i33 = rsqrt_w(d3);
-  T y0 = r[0] * i00;
-  T y1 = (r[1] - l10 * y0) * i11;
-  T y2 = (r[2] - l20 * y0 - l21 * y1) * i22;
-  T y3 = (r[3] - l30 * y0 - l31 * y1 - l32 * y2) * i33;
-  p[3] = y3 * i33;
-  p[2] = (y2 - l32 * p[3]) * i22;
-  p[1] = (y1 - l21 * p[2] - l31 * p[3]) * i11;
-  p[0] = (y0 - l10 * p[1] - l20 * p[2] - l30 * p[3]) * i00;
+  f.i33 = rsqrt_w(d3);
+  return true;
+}
+// p = A^-1 r with the factor of chol4_factor
+template <typename T>
+ACOPF_HD inline void chol4_solve(const Chol4<T>& f, const T r[4], T p[4]) {
+  T y0 = r[0] * f.i00;
+  T y1 = (r[1] - f.l10 * y0) * f.i11;
+  T y2 = (r[2] - f.l20 * y0 - f.l21 * y1) * f.i22;
+  T y3 = (r[3] - f.l30 * y0 - f.l31 * y1 - f.l32 * y2) * f.i33;
+  p[3] = y3 * f.i33;
+  p[2] = (y2 - f.l32 * p[3]) * f.i22;
+  p[1] = (y1 - f.l21 * p[2] - f.l31 * p[3]) * f.i11;
+  p[0] = (y0 - f.l10 * p[1] - f.l20 * p[2] - f.l30 * p[3]) * f.i00;
+}
+// Solve A p = r (A as for chol4_factor).  False on breakdown.
+template <typename T>
+ACOPF_HD inline bool chol4_masked(const T h[10], unsigned fr, const T r[4], T p[4]) {
+  Chol4<T> f;
+  if (!chol4_factor(h, fr, f)) return false;
+  chol4_solve(f, r, p);
   return true;
 }
 
@@ -185,9 +202,10 @@ ACOPF_HD inline int box_qp(const T h[10], const T b[4], const T lo[4], const T h
     else if (x[i] >= hi[i]) { x[i] = hi[i]; fx |= 1u << i; hs |= 1u << i; }
     scale = fmax(scale, fabs(b[i]));
   }
-  T hmax = T(0);
-#pragma unroll
-  for (int k = 0; k < 10; ++k) hmax = fmax(hmax, fabs(h[k]));
+  // max |h_k| as a tree (a shorter chain than a running max)
+  const T m01 = fmax(fabs(h[0]), fabs(h[1])), m23 = fmax(fabs(h[2]), fabs(h[3])), m45 = fmax(fabs(h[4]), fabs(h[5]));
+  const T m67 = fmax(fabs(h[6]), fabs(h[7])), m89 = fmax(fabs(h[8]), fabs(h[9]));
+  const T hmax = fmax(fmax(fmax(m01, m23), fmax(m45, m67)), m89);
   int it = 0;
   for (; it < maxit; ++it) {
     // minimiser over the free variables with the others held at their bounds
@@ -201,7 +219,9 @@ ACOPF_HD inline int box_qp(const T h[10], const T b[4], const T lo[4], const T h
         if ((fx >> j) & 1u) s -= h[pk(i, j)] * x[j];
       rhs[i] = ((fx >> i) & 1u) ? T(0) : s;
     }
-    if (!chol4_masked(h, fr, rhs, y)) break;
+    Chol4<T> fac;
+    if (!chol4_factor(h, fr, fac)) break;
+    chol4_solve(fac, rhs, y);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
       if ((fx >> i) & 1u) y[i] = x[i];
@@ -271,10 +291,10 @@ ACOPF_HD inline int box_qp(const T h[10], const T b[4], const T lo[4], const T h
           T ri = resid_dot2(rhs[i], a, xf);
           rr[i] = ((fx >> i) & 1u) ? T(0) : ri;
         }
-        if (chol4_masked(h, fr, rr, dy))
+        chol4_solve(fac, rr, dy);  // the same factor (the active set is unchanged)
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
-            if (!((fx >> i) & 1u)) x[i] = clampv(x[i] + dy[i], lo[i], hi[i]);
+        for (int i = 0; i < 4; ++i)
+          if (!((fx >> i) & 1u)) x[i] = clampv(x[i] + dy[i], lo[i], hi[i]);
       }
       return it + 1;
     }
@@ -611,12 +631,16 @@ ACOPF_HD inline bool row_on(const LineQP<T>& P, int r) {
 template <typename T>
 ACOPF_HD inline void line_solve(const LineQP<T>& P, T x[4], T u[4], T beta, T alm_tol, int alm_outer, int newton_max,
                                 int* work = nullptr) {
+  // the rows' values at the current x, evaluated once per point
+  T hv[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) hv[r] = row_h(P, r, x);
   for (int outer = 0; outer < alm_outer; ++outer) {
     if (work) work[1]++;
     unsigned pat = 0;
 #pragma unroll
     for (int r = 0; r < 4; ++r)
-      if (row_on(P, r) && u[r] + beta * row_h(P, r, x) > T(0)) pat |= 1u << r;
+      if (row_on(P, r) && u[r] + beta * hv[r] > T(0)) pat |= 1u << r;
     for (int it = 0; it < newton_max; ++it) {
       // pieces fixed: quadratic beta R R' and linear (u - beta rb) R on the rows in pat
       T h[10], b[4];
@@ -649,10 +673,12 @@ ACOPF_HD inline void line_solve(const LineQP<T>& P, T x[4], T u[4], T beta, T al
       }
       int nf = box_qp(h, b, P.lo, P.hi, x, 12);
       if (work) work[0] += nf;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) hv[r] = row_h(P, r, x);
       unsigned np = 0;
 #pragma unroll
       for (int r = 0; r < 4; ++r)
-        if (row_on(P, r) && u[r] + beta * row_h(P, r, x) > T(0)) np |= 1u << r;
+        if (row_on(P, r) && u[r] + beta * hv[r] > T(0)) np |= 1u << r;
       if (np == pat) break;
       pat = np;
     }
@@ -664,7 +690,7 @@ ACOPF_HD inline void line_solve(const LineQP<T>& P, T x[4], T u[4], T beta, T al
         u[r] = T(0);
         continue;
       }
-      T hr = row_h(P, r, x);
+      const T hr = hv[r];
       T un = u[r] + beta * hr;
       un = un > T(0) ? un : T(0);
       const T mb = div_w(-un, beta);
