@@ -449,3 +449,29 @@ def test_cluster_sweep_with_state_in_shared_memory():
     for (ra, oa), (rb, ob) in zip(*out):
         assert ra["result"] == rb["result"], (ra, rb)
         np.testing.assert_allclose(ob, oa, rtol=1e-6)
+
+
+def test_cluster_sweep_with_correction_and_restoration():
+    """The cluster forms under the SQP's second-order correction and
+    feasibility restoration: in a correction pass only the instances whose
+    step was rejected run, so the clusters of the others return at once.  A
+    batch with a grid that restoration certifies infeasible, an overloaded
+    two-bus grid and the 30-bus grid ends the same in the cluster form as in
+    the device-wide form (mixed precision, results to FP32 rounding)."""
+    grids = [gg.batched_uneven()[256 + 7], gg.grid_30bus(),
+             gg.two_bus(lossless=True, pd2=5.0, qd2=0.2, pmax=(2.0, 2.0), rate=10.0)]
+    opts = binding.default_sqp(tol=1e-4, max_sqp=40, soc=1, restore=1,
+                               admm=dict(rho=2e4, max_iter=1000, eps=1e-3, eps_dual=5e-3))
+    out = []
+    for st in (0, 4):
+        s = binding.Solver(grids, precision="mixed")
+        s.tune(256, 0, st)
+        s.sqp_solve_graph(opts, check_every=2)
+        out.append([(s.get_residuals(k), s.get_solution(k)["obj"]) for k in range(len(grids))])
+        s.close()
+    for k, ((ra, oa), (rb, ob)) in enumerate(zip(*out)):
+        assert ra["result_name"] == rb["result_name"], (k, ra, rb)
+        if ra["result_name"] == "converged":
+            np.testing.assert_allclose(ob, oa, rtol=1e-6)
+        else:
+            np.testing.assert_allclose(rb["primal"], ra["primal"], rtol=1e-3)
