@@ -702,4 +702,198 @@ ACOPF_HD inline void line_solve(const LineQP<T>& P, T x[4], T u[4], T beta, T al
   }
 }
 
+
+// ------------------------------------------ exact FP64 line QP by prediction
+// The FP64 line subproblem solved exactly with most of the work in FP32: the
+// augmented Lagrangian in FP32 (from the multipliers u and the point x given)
+// predicts which bounds and rows are active;
+// the equality-constrained QP on that set is solved in FP64 (Cholesky of Q on
+// the free variables, then the rows' multipliers from the Schur complement
+// S = N Q^-1 N'); the KKT conditions are checked in FP64: every free variable
+// within its bounds, every inactive row satisfied, every multiplier of an
+// active row or bound of the right sign, each up to a tolerance of 1e-11 of
+// the problem's scale.  Both solutions are the unique KKT point, so they agree
+// up to rounding.  Returns false when the prediction fails the check and two
+// corrections of the set; the caller then runs the FP64 dual active-set
+// method.  On entry x and u hold a starting point and multipliers.
+ACOPF_HD inline bool line_solve_predicted(const LineQP<double>& P, double x[4], double u[4]) {
+  LineQP<float> F;
+#pragma unroll
+  for (int k = 0; k < 10; ++k) F.q[k] = (float)P.q[k];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    F.c[i] = (float)P.c[i];
+    F.lo[i] = (float)P.lo[i];
+    F.hi[i] = (float)P.hi[i];
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) F.R[r][i] = (float)P.R[r][i];
+    F.rb[r] = (float)P.rb[r];
+    F.on[r] = P.on[r];
+  }
+  F.alo = (float)P.alo;
+  F.ahi = (float)P.ahi;
+  F.ang = P.ang;
+  // the FP32 augmented Lagrangian from the multipliers given and the
+  // unconstrained start clamped into the box
+  float xf[4], uf[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    xf[i] = clampv((float)x[i], F.lo[i], F.hi[i]);
+    uf[i] = (float)u[i];
+  }
+  {
+    const float qd = fmax(fmax(F.q[0], F.q[4]), fmax(F.q[7], F.q[9]));
+    line_solve(F, xf, uf, 10.0f * qd, Tol<float>::alm, 50, 20);
+  }
+  // predicted active set: bounds (at hi when the hs bit is set) and rows; a
+  // bound counts as active when the FP32 point lies within 1e-6 of the box's
+  // width from it (FP32 rounding can leave an active bound a hair inside)
+  unsigned fx = 0, hs = 0, act = 0;
+  double xb[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    xb[i] = 0.0;
+    const float dlt = 1e-6f * (F.hi[i] - F.lo[i]);
+    if (!(P.lo[i] < P.hi[i]) || xf[i] <= F.lo[i] + dlt) {
+      fx |= 1u << i;
+      xb[i] = P.lo[i];
+    } else if (xf[i] >= F.hi[i] - dlt) {
+      fx |= 1u << i;
+      hs |= 1u << i;
+      xb[i] = P.hi[i];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    if (row_on(P, r) && uf[r] > 0.f) act |= 1u << r;
+  // row r: n_r . x <= b_r
+  double n[4][4], b[4];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) n[r][i] = P.R[r][i];
+    b[r] = P.rb[r];
+  }
+  n[2][0] = 0.0; n[2][1] = 1.0; n[2][2] = 0.0; n[2][3] = -1.0; b[2] = P.ahi;
+  n[3][0] = 0.0; n[3][1] = -1.0; n[3][2] = 0.0; n[3][3] = 1.0; b[3] = -P.alo;
+  double cm = 0.0, qm = 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) cm = fmax(cm, fabs(P.c[i]));
+#pragma unroll
+  for (int k = 0; k < 10; ++k) qm = fmax(qm, fabs(P.q[k]));
+  double xs[4], mu[4];
+  bool ok = false;
+  // the predicted set, then at most two corrections of it (bounds and rows
+  // found violated are added, those with a multiplier of the wrong sign
+  // dropped) before giving up
+  for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
+    // minimiser y over the free variables with the rows left out
+    const unsigned fr = ~fx & 15u;
+    Chol4<double> fac;
+    if (!chol4_factor(P.q, fr, fac)) return false;
+    double rhs[4], y[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      double sv = -P.c[i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if ((fx >> j) & 1u) sv -= P.q[pk(i, j)] * xb[j];
+      rhs[i] = ((fx >> i) & 1u) ? 0.0 : sv;
+    }
+    chol4_solve(fac, rhs, y);
+    // W_r = Q_FF^-1 n_r(F) for the active rows, S = N W, t = N y - (b - N xb)
+    double W[4][4], S[10], t[4];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) S[k] = 0.0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      t[r] = 0.0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) W[r][i] = 0.0;
+      if (!((act >> r) & 1u)) continue;
+      double nf[4], bf = b[r];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const bool fixed = (fx >> i) & 1u;
+        nf[i] = fixed ? 0.0 : n[r][i];
+        if (fixed) bf -= n[r][i] * xb[i];
+      }
+      chol4_solve(fac, nf, W[r]);
+      double ny = 0.0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) ny += nf[i] * y[i];
+      t[r] = ny - bf;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = r; q < 4; ++q) {
+        if (!((act >> r) & 1u) || !((act >> q) & 1u)) continue;
+        double v = 0.0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v += ((fx >> i) & 1u) ? 0.0 : n[r][i] * W[q][i];
+        S[pk(r, q)] = v;
+      }
+    Chol4<double> fs;
+    if (!chol4_factor(S, act, fs)) return false;
+    chol4_solve(fs, t, mu);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      double v = ((fx >> i) & 1u) ? xb[i] : y[i];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if ((act >> r) & 1u) v -= mu[r] * W[r][i];
+      xs[i] = ((fx >> i) & 1u) ? xb[i] : v;
+    }
+    // KKT check: gradient of the Lagrangian g = Q x + c + sum_r mu_r n_r
+    double g[4];
+    symv4(P.q, xs, g);
+    double xm = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      g[i] += P.c[i];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if ((act >> r) & 1u) g[i] += mu[r] * n[r][i];
+      xm = fmax(xm, fabs(xs[i]));
+    }
+    const double tol = 1e-11 * (cm + qm * xm + 1.0), tx = 1e-11 * (xm + 1.0);
+    unsigned nfx = fx, nhs = hs, nact = act;
+    ok = true;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if ((act >> r) & 1u) {
+        if (!(mu[r] >= -tol)) { ok = false; nact &= ~(1u << r); }
+      } else if (row_on(P, r)) {
+        double v = -b[r];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v += n[r][i] * xs[i];
+        if (!(v <= tx * (1.0 + fabs(b[r])))) { ok = false; nact |= 1u << r; }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (!((fx >> i) & 1u)) {
+        if (!(xs[i] >= P.lo[i] - tx)) { ok = false; nfx |= 1u << i; nhs &= ~(1u << i); xb[i] = P.lo[i]; }
+        else if (!(xs[i] <= P.hi[i] + tx)) { ok = false; nfx |= 1u << i; nhs |= 1u << i; xb[i] = P.hi[i]; }
+      } else if (P.lo[i] < P.hi[i]) {
+        if (!(((hs >> i) & 1u) ? g[i] <= tol : g[i] >= -tol)) { ok = false; nfx &= ~(1u << i); xb[i] = 0.0; }
+      }
+    }
+    if (!ok && nfx == fx && nhs == hs && nact == act) return false;  // nothing to correct (non-finite values)
+    fx = nfx;
+    hs = nhs;
+    act = nact;
+  }
+  if (!ok) return false;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x[i] = clampv(xs[i], P.lo[i], P.hi[i]);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) u[r] = ((act >> r) & 1u) && mu[r] > 0.0 ? mu[r] : 0.0;
+  return true;
+}
+
 }  // namespace acopf

@@ -180,7 +180,15 @@ __device__ __forceinline__ void gen_phase(const SweepP<T>& p, int g, float sc) {
   gen_compute(d, g, a, b);
 }
 
-// the augmented Lagrangian as a call of its own in the FP64 sweep (see line_compute)
+// the FP64 line solves as calls of their own (see line_compute): the
+// predicted active set, the dual method when the prediction fails its check,
+// and the augmented Lagrangian for a subproblem with no feasible point
+__device__ __noinline__ bool line_pred_call(const LineQP<double>& P, double* x, double* u) {
+  return line_solve_predicted(P, x, u);
+}
+__device__ __noinline__ int line_exact_call(const LineQP<double>& P, double* x, double* u) {
+  return line_solve_exact(P, x, u);
+}
 template <typename T>
 __device__ __noinline__ void line_alm_call(const LineQP<T>& P, T* x, T* u, T beta, T tol, int outer, int newton) {
   line_solve(P, x, u, beta, tol, outer, newton);
@@ -297,13 +305,14 @@ __device__ __forceinline__ void line_compute_to(const SweepP<T>& p, int l, const
   for (int i = 0; i < 4; ++i) x[i] = clampv(zv[i], P.lo[i], P.hi[i]);
   const T beta = p.beta_scale * fmax(fmax(P.q[0], P.q[4]), fmax(P.q[7], P.q[9]));
   if constexpr (sizeof(T) == 8) {
-    // FP64 sweep: the exact dual active-set method by default (the augmented
-    // Lagrangian, called out of line, for line_solver = 1 and for a
-    // subproblem with no feasible point: it treats the rows softly)
+    // FP64 sweep: the exact solution by default -- the active set predicted in
+    // FP32 and the KKT point solved and checked in FP64, else the dual
+    // active-set method; the augmented Lagrangian for line_solver = 1 and for
+    // a subproblem with no feasible point (it treats the rows softly)
     bool alm = !p.line_exact;
-    if (p.line_exact) {
+    if (p.line_exact && !line_pred_call(P, x, u)) {
       const T u_in[4] = {u[0], u[1], u[2], u[3]};
-      if (line_solve_exact(P, x, u) < 0) {
+      if (line_exact_call(P, x, u) < 0) {
         alm = true;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
