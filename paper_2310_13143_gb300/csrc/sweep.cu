@@ -486,15 +486,25 @@ __device__ __forceinline__ void entry_load(const Dev& d, int c, V4<T>& x, V4<T>&
 // contributions to the bus sums: c = lambda + rho x per coupling; the 2x2
 // matrix sums 1/rho over every coupled flow, generators enter with +, branch
 // ends with - (they draw power from the bus)
+// a / r: in FP64 the product with one reciprocal of r (a correctly rounded
+// division costs many FP64 instructions on GB300, whose FP64 rate is a small
+// fraction of FP32); in FP32 the special-function quotient
+template <typename T>
+__device__ __forceinline__ T over_r(T a, T r, T ir) {
+  if constexpr (sizeof(T) == 8) return a * ir;
+  else return div_w(a, r);
+}
+
 template <typename T>
 __device__ __forceinline__ void entry_sums(int c, const V4<T>& x, const V4<T>& lm, T r, T* S) {
-  S[0] += div_w(T(1), r);
+  const T ir = div_w(T(1), r);
+  S[0] += ir;
   if (c < 0) {
-    S[1] += div_w(lm.x + r * x.x, r);
-    S[2] += div_w(lm.y + r * x.y, r);
+    S[1] += over_r(lm.x + r * x.x, r, ir);
+    S[2] += over_r(lm.y + r * x.y, r, ir);
   } else {
-    S[1] -= div_w(lm.x + r * x.x, r);
-    S[2] -= div_w(lm.y + r * x.y, r);
+    S[1] -= over_r(lm.x + r * x.x, r, ir);
+    S[2] -= over_r(lm.y + r * x.y, r, ir);
     S[3] += r;
     S[4] += lm.z + r * x.z;
     S[5] += lm.w + r * x.w;
@@ -513,10 +523,11 @@ __device__ __forceinline__ void bus_values(V4<T> br, int isref, const T* S, T& n
   const T v1 = S[1] - gsh * S[4] * iQw - br.x;
   const T v2 = S[2] + bsh * S[4] * iQw - br.y;
   const T det = M11 * M22 - M12 * M12;
-  n1 = div_w(M22 * v1 - M12 * v2, det);
-  n2 = div_w(M11 * v2 - M12 * v1, det);
+  const T idet = sizeof(T) == 8 ? div_w(T(1), det) : T(0);
+  n1 = over_r(M22 * v1 - M12 * v2, det, idet);
+  n2 = over_r(M11 * v2 - M12 * v1, det, idet);
   dw = (S[4] + gsh * n1 - bsh * n2) * iQw;
-  dth = (isref || !(S[3] > T(0))) ? T(0) : div_w(S[5], S[3]);
+  dth = (isref || !(S[3] > T(0))) ? T(0) : over_r(S[5], S[3], iQw);
 }
 
 template <typename T>
@@ -548,9 +559,10 @@ __device__ __forceinline__ void entry_store(const Dev& d, int c, const V4<T>& zn
 template <typename T>
 __device__ __forceinline__ void entry_values(int c, const V4<T>& x, const V4<T>& lm, const V4<T>& zo, T r, T n1, T n2,
                                              T dw, T dth, T& rm, T& sm, V4<T>& zn, V4<T>& ln) {
+  const T ir = sizeof(T) == 8 ? div_w(T(1), r) : T(0);
   if (c < 0) {
-    zn.x = div_w(lm.x + r * x.x - n1, r);
-    zn.y = div_w(lm.y + r * x.y - n2, r);
+    zn.x = over_r(lm.x + r * x.x - n1, r, ir);
+    zn.y = over_r(lm.y + r * x.y - n2, r, ir);
     zn.z = zn.w = T(0);
     sm = fmax(sm, r * fmax(fabs(zn.x - zo.x), fabs(zn.y - zo.y)));
     const T rx = x.x - zn.x, ry = x.y - zn.y;
@@ -559,8 +571,8 @@ __device__ __forceinline__ void entry_values(int c, const V4<T>& x, const V4<T>&
     ln.y = lm.y + r * ry;
     ln.z = ln.w = T(0);
   } else {
-    zn.x = div_w(lm.x + r * x.x + n1, r);
-    zn.y = div_w(lm.y + r * x.y + n2, r);
+    zn.x = over_r(lm.x + r * x.x + n1, r, ir);
+    zn.y = over_r(lm.y + r * x.y + n2, r, ir);
     zn.z = dw;
     zn.w = dth;
     const T a1 = fmax(fabs(zn.x - zo.x), fabs(zn.y - zo.y));
