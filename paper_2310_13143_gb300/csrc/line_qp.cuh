@@ -53,7 +53,25 @@ ACOPF_HD inline float div_w(float a, float b) {
   return a / b;
 #endif
 }
-ACOPF_HD inline double rsqrt_w(double a) { return 1.0 / sqrt(a); }
+// 1/sqrt(a) in FP64 from an estimate y0 refined by two Newton-Raphson steps
+// on f(y) = 1/y^2 - a:  y <- y (3 - a y^2) / 2.  A relative error e becomes
+// about -3/2 e^2 per step, so an FP32 estimate (|e| <= 2^-21) ends below
+// FP64 rounding after two steps.  On the device the estimate is the FP32
+// special-function unit's rsqrtf; a correctly rounded square root and
+// division cost many FP64 instructions on GB300, whose FP64 rate is a small
+// fraction of FP32.
+ACOPF_HD inline double rsqrt_newton(double a, double y0) {
+  double y = y0;
+  y = y * (1.5 - 0.5 * a * y * y);
+  y = y * (1.5 - 0.5 * a * y * y);
+  return y;
+}
+ACOPF_HD inline double rsqrt_w(double a) {
+#ifdef __CUDA_ARCH__
+  if (a > 1e-30 && a < 1e30) return rsqrt_newton(a, (double)rsqrtf((float)a));
+#endif
+  return 1.0 / sqrt(a);
+}
 ACOPF_HD inline float rsqrt_w(float a) {
 #ifdef __CUDA_ARCH__
   return rsqrtf(a);
@@ -709,10 +727,10 @@ ACOPF_HD inline void line_solve(const LineQP<T>& P, T x[4], T u[4], T beta, T al
 // predicts which bounds and rows are active;
 // the equality-constrained QP on that set is solved in FP64 (Cholesky of Q on
 // the free variables, then the rows' multipliers from the Schur complement
-// S = N Q^-1 N'); the KKT conditions are checked in FP64: every free variable
-// within its bounds, every inactive row satisfied, every multiplier of an
-// active row or bound of the right sign, each up to a tolerance of 1e-11 of
-// the problem's scale.  Both solutions are the unique KKT point, so they agree
+// S = N Q^-1 N'); the KKT conditions are checked in FP64: the Lagrangian
+// stationary in the free variables, every free variable within its bounds,
+// every row satisfied, every multiplier of an active row or bound of the
+// right sign, each up to a tolerance of 1e-11 of the problem's scale.  Both solutions are the unique KKT point, so they agree
 // up to rounding.  Returns false when the prediction fails the check and two
 // corrections of the set; the caller then runs the FP64 dual active-set
 // method.  On entry x and u hold a starting point and multipliers.
@@ -865,18 +883,23 @@ ACOPF_HD inline bool line_solve_predicted(const LineQP<double>& P, double x[4], 
     ok = true;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
+      if (!row_on(P, r)) continue;
+      double v = -b[r];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v += n[r][i] * xs[i];
+      const bool feas = v <= tx * (1.0 + fabs(b[r]));  // every row, active or not (a singular S shows here)
       if ((act >> r) & 1u) {
         if (!(mu[r] >= -tol)) { ok = false; nact &= ~(1u << r); }
-      } else if (row_on(P, r)) {
-        double v = -b[r];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) v += n[r][i] * xs[i];
-        if (!(v <= tx * (1.0 + fabs(b[r])))) { ok = false; nact |= 1u << r; }
+        if (!feas) ok = false;
+      } else if (!feas) {
+        ok = false;
+        nact |= 1u << r;
       }
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       if (!((fx >> i) & 1u)) {
+        if (!(fabs(g[i]) <= tol)) ok = false;  // stationary in the free variables
         if (!(xs[i] >= P.lo[i] - tx)) { ok = false; nfx |= 1u << i; nhs &= ~(1u << i); xb[i] = P.lo[i]; }
         else if (!(xs[i] <= P.hi[i] + tx)) { ok = false; nfx |= 1u << i; nhs |= 1u << i; xb[i] = P.hi[i]; }
       } else if (P.lo[i] < P.hi[i]) {
