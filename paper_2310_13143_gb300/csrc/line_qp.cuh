@@ -210,12 +210,25 @@ struct Dot2Acc {
 // variable i held at a bound (at lo when bit i of hiside is clear).  Returns
 // the number of factorisations used.
 template <typename T>
-ACOPF_HD inline int box_qp(const T h[10], const T b[4], const T lo[4], const T hi[4], T x[4], int maxit) {
+ACOPF_HD inline int box_qp(const T h[10], const T b[4], const T lo[4], const T hi[4], T x[4], int maxit,
+                           unsigned* wset = nullptr) {
   unsigned fx = 0, hs = 0, perm = 0;
   T scale = T(0);
+  // a warm start: the bounds held at the end of a previous solve (bit 8 set
+  // when *wset holds a set: bits 0-3 held, bits 4-7 at the upper bound)
+  const unsigned ws = wset ? *wset : 0u;
+  const bool warm = (ws >> 8) & 1u;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     if (!(lo[i] < hi[i])) { x[i] = lo[i]; fx |= 1u << i; perm |= 1u << i; }
+    else if (warm) {
+      if ((ws >> i) & 1u) {
+        fx |= 1u << i;
+        if ((ws >> (4 + i)) & 1u) { x[i] = hi[i]; hs |= 1u << i; } else { x[i] = lo[i]; }
+      } else {
+        x[i] = clampv(x[i], lo[i], hi[i]);
+      }
+    }
     else if (x[i] <= lo[i]) { x[i] = lo[i]; fx |= 1u << i; }
     else if (x[i] >= hi[i]) { x[i] = hi[i]; fx |= 1u << i; hs |= 1u << i; }
     scale = fmax(scale, fabs(b[i]));
@@ -314,11 +327,13 @@ ACOPF_HD inline int box_qp(const T h[10], const T b[4], const T lo[4], const T h
         for (int i = 0; i < 4; ++i)
           if (!((fx >> i) & 1u)) x[i] = clampv(x[i] + dy[i], lo[i], hi[i]);
       }
+      if (wset) *wset = 0x100u | fx | (hs << 4);
       return it + 1;
     }
     fx &= ~(1u << worst);
     hs &= ~(1u << worst);
   }
+  if (wset) *wset = 0x100u | fx | (hs << 4);
   return it;
 }
 
@@ -648,7 +663,7 @@ ACOPF_HD inline bool row_on(const LineQP<T>& P, int r) {
 
 template <typename T>
 ACOPF_HD inline void line_solve(const LineQP<T>& P, T x[4], T u[4], T beta, T alm_tol, int alm_outer, int newton_max,
-                                int* work = nullptr) {
+                                int* work = nullptr, unsigned* wset = nullptr) {
   // the rows' values at the current x, evaluated once per point
   T hv[4];
 #pragma unroll
@@ -689,7 +704,7 @@ ACOPF_HD inline void line_solve(const LineQP<T>& P, T x[4], T u[4], T beta, T al
         h[9] += qq;
         h[6] -= qq;
       }
-      int nf = box_qp(h, b, P.lo, P.hi, x, 12);
+      int nf = box_qp(h, b, P.lo, P.hi, x, 12, wset);
       if (work) work[0] += nf;
 #pragma unroll
       for (int r = 0; r < 4; ++r) hv[r] = row_h(P, r, x);

@@ -255,24 +255,30 @@ __device__ __noinline__ T rb_rescale(const Dev& d, int l, float sc, V4<T>* rs, i
 // low.  z, lambda, u and rho are passed in.
 template <typename T, typename Rec, typename Out>
 __device__ __forceinline__ void line_compute_to(const SweepP<T>& p, int l, const Rec& rec, V4<T> z0, V4<T> z1,
-                                                V4<T> l0, V4<T> l1, V4<T> uu, T rho, Out out);
+                                                V4<T> l0, V4<T> l1, V4<T> uu, T rho, Out out, unsigned* wset = nullptr);
 
 template <typename T, typename Rec>
 __device__ __forceinline__ void line_compute(const SweepP<T>& p, int l, const Rec& rec, V4<T> z0, V4<T> z1, V4<T> l0,
-                                             V4<T> l1, V4<T> uu, T rho) {
-  line_compute_to(p, l, rec, z0, z1, l0, l1, uu, rho, [&](const V4<T>& o0, const V4<T>& o1, const V4<T>& ou) {
-    V4<T>* X = (V4<T>*)p.d.X;
-    X[2 * l] = o0;
-    X[2 * l + 1] = o1;
-    ((V4<T>*)p.d.U)[l] = ou;
-  });
+                                             V4<T> l1, V4<T> uu, T rho, unsigned* wset = nullptr) {
+  line_compute_to(
+      p, l, rec, z0, z1, l0, l1, uu, rho,
+      [&](const V4<T>& o0, const V4<T>& o1, const V4<T>& ou) {
+        V4<T>* X = (V4<T>*)p.d.X;
+        X[2 * l] = o0;
+        X[2 * l + 1] = o1;
+        ((V4<T>*)p.d.U)[l] = ou;
+      },
+      wset);
 }
 
 // the line update of branch l; out(o0, o1, ou) receives the couplings of its
 // two ends and its line-limit multipliers
+// wset (FP32 sweep, may be null): the box bounds held at the end of this
+// branch's previous solve, the start of the next one's (a thread that keeps
+// its branch from one ADMM iteration to the next holds it in a register)
 template <typename T, typename Rec, typename Out>
 __device__ __forceinline__ void line_compute_to(const SweepP<T>& p, int l, const Rec& rec, V4<T> z0, V4<T> z1,
-                                                V4<T> l0, V4<T> l1, V4<T> uu, T rho, Out out) {
+                                                V4<T> l0, V4<T> l1, V4<T> uu, T rho, Out out, unsigned* wset) {
   const Dev& d = p.d;
   // couplings: flows p_ij q_ij p_ji q_ji (F rows 0..3), voltages dbar 0..3
   const T zf[4] = {z0.x, z0.y, z1.x, z1.y}, lf[4] = {l0.x, l0.y, l1.x, l1.y};
@@ -324,7 +330,7 @@ __device__ __forceinline__ void line_compute_to(const SweepP<T>& p, int l, const
     if (alm) line_alm_call(P, x, u, beta, p.alm_tol, p.alm_outer, p.newton_max);
   } else {
     // FP32 sweep: the augmented Lagrangian with refinement (Sec. IV-B)
-    line_solve(P, x, u, beta, p.alm_tol, p.alm_outer, p.newton_max);
+    line_solve(P, x, u, beta, p.alm_tol, p.alm_outer, p.newton_max, nullptr, wset);
   }
   // flows at the solution (F and f0 read again)
   T xf[4];
@@ -818,6 +824,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && !RES) ? 2 : 1) k_sweep
   int my_k = -1;
   V4<T> rr[kRecChunks];
   T my_rho = T(0);
+  unsigned my_wset = 0u;  // the box bounds held at the end of the branch's last solve
   TaskStatic<T> ta, tb;
   if (RES) {
     if (tid < d.G) {
@@ -852,7 +859,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && !RES) ? 2 : 1) k_sweep
           const V4<T>* Z = (const V4<T>*)d.Z;
           const V4<T>* LM = (const V4<T>*)d.LAM;
           line_compute(p, l, RRec<T>{rr}, Z[2 * l], Z[2 * l + 1], LM[2 * l], LM[2 * l + 1], ((const V4<T>*)d.U)[l],
-                       my_rho);
+                       my_rho, &my_wset);
         }
       }
     } else if (!kTiled) {
@@ -1069,6 +1076,7 @@ __global__ void __launch_bounds__(256, 1) k_sweep_cluster(SweepP<T> p) {
   // RES: this thread's generator or branch record, this warp's two tasks
   V4<T> rr[kRecChunks];
   T my_rho = T(0);
+  unsigned my_wset = 0u;  // the box bounds held at the end of the branch's last solve
   TaskStatic<T> ta, tb;
   if (RES) {
     if (ct < nG) {
@@ -1100,7 +1108,7 @@ __global__ void __launch_bounds__(256, 1) k_sweep_cluster(SweepP<T> p) {
         const V4<T>* Z = (const V4<T>*)d.Z;
         const V4<T>* LM = (const V4<T>*)d.LAM;
         line_compute(p, l, RRec<T>{rr}, Z[2 * l], Z[2 * l + 1], LM[2 * l], LM[2 * l + 1], ((const V4<T>*)d.U)[l],
-                     my_rho);
+                     my_rho, &my_wset);
       }
     } else {
       int u = ct;
@@ -1290,6 +1298,7 @@ __global__ void __launch_bounds__(256, 1) k_sweep_cluster_dsm(SweepP<T> p) {
   const int g = g0 + ct, l = l0 + ct - nG;
   V4<T> rr[kRecChunks];
   T my_rho = T(0);
+  unsigned my_wset = 0u;  // the box bounds held at the end of the branch's last solve
   V4<T> uu = {T(0), T(0), T(0), T(0)};
   const V4<T> zero4 = {T(0), T(0), T(0), T(0)};
   if (is_gen) {
@@ -1358,7 +1367,8 @@ __global__ void __launch_bounds__(256, 1) k_sweep_cluster_dsm(SweepP<T> p) {
                         x0 = o0;
                         x1 = o1;
                         uu = ou;
-                      });
+                      },
+                      &my_wset);
     }
     if (prof) { tp1 = gtimer(); atomicAdd(&d.phase_ns[0], tp1 - tp0); }
     cluster_barrier();

@@ -438,7 +438,9 @@ def test_cluster_sweep_with_state_in_shared_memory():
             for key in ("x", "z", "lam", "xg", "zg", "lg", "zb", "nu", "ul"):
                 np.testing.assert_allclose(b[key], a[key], rtol=0, atol=1e-4 * max(1.0, np.abs(a[key]).max()),
                                            err_msg=f"{bt}:{st}:{key}")
-    opts = binding.default_sqp(tol=1e-4, max_sqp=8, admm=dict(rho=2e4, max_iter=600, eps=1e-4, eps_dual=5e-3))
+    # enough SQP iterations that no instance sits at the limit: which side of
+    # it an FP32 run ends on is a matter of rounding
+    opts = binding.default_sqp(tol=1e-4, max_sqp=20, admm=dict(rho=2e4, max_iter=600, eps=1e-4, eps_dual=5e-3))
     out = []
     for st in (0, 4):
         s = binding.Solver(grids, precision="mixed")
