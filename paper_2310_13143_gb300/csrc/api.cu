@@ -435,7 +435,7 @@ acopf_status acopf_create(const acopf_grid* grids, int32_t ngrids, const acopf_o
   A(d.pd, B); A(d.qd, B); A(d.gs, B); A(d.bs, B); A(d.wmin, B); A(d.wmax, B); A(d.isref, B);
   A(d.end_ptr, B + 1); A(d.end_idx, 2 * (size_t)L); A(d.gen_ptr, B + 1);
   A(d.ent, E); A(d.ebus, E); A(d.pent, pent.size()); A(d.pbus, pbus.size()); A(d.pinst, pinst.size());
-  A(d.big, big.size()); A(d.task_off, K + 1); A(d.big_off, K + 1);
+  A(d.big, big.size()); A(d.task_off, K + 1); A(d.big_off, K + 1); A(d.wset, L);
   d.E = (int)E;
   d.NT = (int)(pbus.size() / 32);
   d.NBIG = (int)(big.size() / 2);

@@ -94,6 +94,12 @@ struct Dev {
   int *pent, *pbus, *pinst;
   int* big;
   int E, NT, NBIG;
+  // per branch: the box bounds held at the end of its last FP32 line solve in
+  // a resident sweep form (bit 8: set held; bits 0-3 held, 4-7 at the upper
+  // bound), the start of the next launch's first solve; cleared when the QP
+  // is built.  (The streaming forms start each solve from the clamped point:
+  // the extra load and store cost more there than the saved factorisations.)
+  uint16_t* wset;
   // first warp task and first big task of every instance (K + 1 each); no
   // task holds buses of two instances
   int *task_off, *big_off;

@@ -160,6 +160,7 @@ __global__ void k_build_branch(Dev d, int use_angle, double* xbr, int pass) {
   if (l >= d.L) return;
   int k = d.br_inst[l];
   if (!live(d.ctl[k], pass)) return;
+  d.wset[l] = 0;  // a new QP: no active set carried over
   double delta = d.ctl[k].delta;
   double rho = d.rho_l[l];
   Br b;

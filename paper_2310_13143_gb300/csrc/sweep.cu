@@ -837,6 +837,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && !RES) ? 2 : 1) k_sweep
 #pragma unroll
       for (int c = 0; c < kRecChunks; ++c) rr[c] = ((const V4<T>*)d.lrec)[(size_t)c * d.L + l];
       my_rho = ((const T*)d.trho_l)[l];
+      my_wset = d.wset[l];
     }
     ta = task_static<T>(d, wid < d.NT ? load_slot(d, wid, lane) : none);
     tb = task_static<T>(d, wid + nw < d.NT ? load_slot(d, wid + nw, lane) : none);
@@ -1001,6 +1002,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && !RES) ? 2 : 1) k_sweep
     if (prof) atomicAdd(&d.phase_ns[3], gtimer() - tp1);
     if (all && !p.fixed) { ++it; break; }
   }
+  if (RES && sizeof(T) == 4 && tid >= d.G && tid < d.G + d.L) d.wset[tid - d.G] = (uint16_t)my_wset;
   // record the residuals of unfinished instances
   if (blockIdx.x == 0 && !aborted) {
     int last = (it - 1) & 1;
@@ -1087,6 +1089,7 @@ __global__ void __launch_bounds__(256, 1) k_sweep_cluster(SweepP<T> p) {
 #pragma unroll
       for (int c = 0; c < kRecChunks; ++c) rr[c] = ((const V4<T>*)d.lrec)[(size_t)c * d.L + l];
       my_rho = ((const T*)d.trho_l)[l];
+      my_wset = d.wset[l];
     }
     ta = task_static<T>(d, t0 + cw < t1 ? load_slot(d, t0 + cw, lane) : none);
     tb = task_static<T>(d, t0 + cw + nwc < t1 ? load_slot(d, t0 + cw + nwc, lane) : none);
@@ -1161,6 +1164,7 @@ __global__ void __launch_bounds__(256, 1) k_sweep_cluster(SweepP<T> p) {
       break;
     }
   }
+  if (RES && sizeof(T) == 4 && ct >= nG && l0 + ct - nG < l1) d.wset[l0 + ct - nG] = (uint16_t)my_wset;
   if (rank == 0 && threadIdx.x == 0) {
     if (conv) d.admm_done[k] = 1;
     d.admm_iters[k] = it;
@@ -1311,6 +1315,7 @@ __global__ void __launch_bounds__(256, 1) k_sweep_cluster_dsm(SweepP<T> p) {
 #pragma unroll
     for (int c = 0; c < kRecChunks; ++c) rr[c] = ((const V4<T>*)d.lrec)[(size_t)c * d.L + l];
     my_rho = ((const T*)d.trho_l)[l];
+    my_wset = d.wset[l];
     uu = ((const V4<T>*)d.U)[l];
     s_zl[4 * j] = ((const V4<T>*)d.Z)[2 * l];
     s_zl[4 * j + 1] = ((const V4<T>*)d.LAM)[2 * l];
@@ -1413,6 +1418,7 @@ __global__ void __launch_bounds__(256, 1) k_sweep_cluster_dsm(SweepP<T> p) {
       ((V4<T>*)d.X)[2 * l] = x0;
       ((V4<T>*)d.X)[2 * l + 1] = x1;
       ((V4<T>*)d.U)[l] = uu;
+      d.wset[l] = (uint16_t)my_wset;
     }
     if (A.st.s.bus >= 0) entry_store(d, A.st.s.code, A.zo, A.lm);
     if (B.st.s.bus >= 0) entry_store(d, B.st.s.code, B.zo, B.lm);
