@@ -372,7 +372,7 @@ acopf_status acopf_tune(acopf_handle h, int32_t block_threads, int32_t ctas_per_
  * JSON file holding an entry for this handle's key -- SM count, sweep
  * precision and the binary orders of magnitude of the instance, bus and
  * branch counts -- that shape is applied.  Otherwise the QP at the current
- * iterate is built (delta 1, rho 2e4) and every shape of {64, 128, 256}
+ * iterate is built (delta 1, rho 2e4) and every shape of {64, 128, 192, 224, 256}
  * threads x {as many CTAs per SM as fit, 1} x record access {0, 1, 2, 3, 4}
  * (FP32 sweep; FP64: {0, 3, 4}, see acopf_tune) is timed over iters fixed ADMM iterations with CUDA
  * events; the fastest is applied and written to the cache (other keys are

@@ -931,7 +931,7 @@ static std::string tune_key(Ctx* c) {
     return k;
   };
   char buf[128];
-  snprintf(buf, sizeof(buf), "v3-sm%d-%s-K%d-B%d-L%d", c->num_sms, c->precision == ACOPF_MIXED ? "mixed" : "fp64",
+  snprintf(buf, sizeof(buf), "v4-sm%d-%s-K%d-B%d-L%d", c->num_sms, c->precision == ACOPF_MIXED ? "mixed" : "fp64",
            lg(c->d.K), lg(c->d.B), lg(c->d.L));
   return buf;
 }
@@ -1013,13 +1013,13 @@ acopf_status acopf_autotune(acopf_handle h, const char* cache_path, int32_t iter
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const int threads[3] = {64, 128, 256};
+    const int threads[5] = {64, 128, 192, 224, 256};
     // record access: in place (0), staged tiles (1, 2; FP32 sweep only), held
     // in registers (3); one thread-block cluster per instance (4)
     const int modes_mixed[5] = {0, 1, 2, 3, 4}, modes_fp64[3] = {0, 3, 4};
     const int* modes = c->precision == ACOPF_MIXED ? modes_mixed : modes_fp64;
     const int nmodes = c->precision == ACOPF_MIXED ? 5 : 3;
-    for (int ti = 0; ti < 3; ++ti)
+    for (int ti = 0; ti < 5; ++ti)
       for (int cps = 0; cps <= 1; ++cps)
         for (int mi = 0; mi < nmodes; ++mi) {
           const int st = modes[mi];

@@ -297,7 +297,7 @@ def test_autotune_applies_and_caches_a_shape(tmp_path):
     grids = [gg.grid_30bus()] * 4
     s = binding.Solver(grids, precision="mixed")
     shape, us = s.autotune(cache, iters=20)
-    assert shape[0] in (64, 128, 256) and shape[1] in (0, 1) and shape[2] in (0, 1, 2, 3, 4) and us > 0
+    assert shape[0] in (64, 128, 192, 224, 256) and shape[1] in (0, 1) and shape[2] in (0, 1, 2, 3, 4) and us > 0
     import json
     entries = json.load(open(cache))
     assert len(entries) == 1 and entries[0]["block_threads"] == shape[0]
