@@ -8,8 +8,8 @@ final iterate, multipliers and ADMM state of cold-start solves of sampled
 scenarios, computed by the same solver, and penalty factors chosen by
 solving each scenario from the network's own predicted start under a few
 candidate factors (rho_targets).  A warm-started solve must still pass the
-solver's own convergence test, so the cold-start method remains the judge
-of the prediction's error.
+solver's own convergence test, so the cold-start method still decides
+whether a prediction was good enough.
 
 Everything numeric runs in the library's kernels (solves, tensor-core
 products, Adam, the scatter into the solver); this module only moves arrays

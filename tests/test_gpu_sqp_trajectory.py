@@ -69,7 +69,7 @@ def test_sqp_history_matches_oracle(name, cluster):
     m = oracle.Model(g)
     line_fail = []
     want = alg1(m, o, line_fail)
-    np.testing.assert_array_equal(want, m.sqp(o)["hist"])  # the driver is the oracle's own loop
+    np.testing.assert_array_equal(want, m.sqp(o)["hist"])  # the second loop of Alg. 1 equals the oracle's own
     s = binding.Solver(g, precision="fp64")
     if cluster:
         s.tune(256, 0, 4)
