@@ -812,11 +812,14 @@ ACOPF_HD inline bool line_solve_predicted(const LineQP<double>& P, double x[4], 
   }
   n[2][0] = 0.0; n[2][1] = 1.0; n[2][2] = 0.0; n[2][3] = -1.0; b[2] = P.ahi;
   n[3][0] = 0.0; n[3][1] = -1.0; n[3][2] = 0.0; n[3][3] = 1.0; b[3] = -P.alo;
-  double cm = 0.0, qm = 0.0;
+  // the scales of the tolerances below, from the FP32 copy (a relative
+  // error of 1e-7 in a tolerance does not matter; FP32 costs far less)
+  float cmf = 0.f, qmf = 0.f;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) cm = fmax(cm, fabs(P.c[i]));
+  for (int i = 0; i < 4; ++i) cmf = fmax(cmf, fabs(F.c[i]));
 #pragma unroll
-  for (int k = 0; k < 10; ++k) qm = fmax(qm, fabs(P.q[k]));
+  for (int k = 0; k < 10; ++k) qmf = fmax(qmf, fabs(F.q[k]));
+  const double cm = cmf, qm = qmf;
   double xs[4], mu[4];
   bool ok = false;
   // the predicted set, then at most two corrections of it (bounds and rows

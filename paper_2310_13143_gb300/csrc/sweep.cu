@@ -742,6 +742,35 @@ __device__ __forceinline__ void bus_task_pair(const Dev& d, const TaskData<T>& a
   res_max2_pair(dst, rma, sma, a.s.inst, rmb, smb, b.s.inst);
 }
 
+// one task alone in its warp.  The FP64 sweep gives each warp one task where
+// the launch allows it: FP64 arithmetic issues at a small fraction of the
+// FP32 rate in each SM partition, so two tasks interleaved in one warp take
+// about twice as long as one, where in FP32 they overlap.  The arithmetic is
+// that of task a of bus_task_pair.  All 32 lanes call it.
+template <typename T>
+__device__ __forceinline__ void bus_task_one(const Dev& d, const TaskData<T>& a, const ResDst& dst) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  T S[6] = {0, 0, 0, 0, 0, 0};
+  if (a.s.bus >= 0) entry_sums(a.s.code, a.x, a.lm, a.r, S);
+  seg_scan(a.s.bus, S);
+  T n1 = 0, n2 = 0, dw = 0, dt = 0;
+  if (a.last) bus_solve(d, a.s.bus, a.br, a.isref, S, n1, n2, dw, dt);
+  const unsigned h = __ballot_sync(FULL, a.last) >> lane;
+  const int src = h ? lane + __ffs(h) - 1 : lane;
+  n1 = __shfl_sync(FULL, n1, src);
+  n2 = __shfl_sync(FULL, n2, src);
+  dw = __shfl_sync(FULL, dw, src);
+  dt = __shfl_sync(FULL, dt, src);
+  T rm = T(0), sm = T(0);
+  if (a.s.bus >= 0) {
+    entry_update(d, a.s.code, a.x, a.lm, a.zo, a.r, n1, n2, dw, dt, rm, sm);
+    if (!(rm == rm)) rm = T(1e30);
+    if (!(sm == sm)) sm = T(1e30);
+  }
+  res_max2(dst, rm, sm, a.s.inst);
+}
+
 // one bus with more than 32 entries (entries [q0, q1) of ent); lanes loop
 template <typename T, bool kDone = true>
 __device__ void bus_task_big(const SweepP<T>& p, int q0, int q1, const ResDst& dst, const int* s_done) {
@@ -945,7 +974,11 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && !RES) ? 2 : 1) k_sweep
     // what the current tasks write); loop bounds are uniform per warp so that
     // all lanes reduce together
     if (RES) {
-      if (wid < d.NT) bus_task_pair(d, task_load<T>(d, ta, s_done), task_load<T>(d, tb, s_done), dst);
+      if (sizeof(T) == 8 && nw >= d.NT) {  // FP64, one task per warp
+        if (wid < d.NT) bus_task_one(d, task_load<T>(d, ta, s_done), dst);
+      } else if (wid < d.NT) {
+        bus_task_pair(d, task_load<T>(d, ta, s_done), task_load<T>(d, tb, s_done), dst);
+      }
       for (int b = wid; b < d.NBIG; b += nw) bus_task_big(p, d.big[2 * b], d.big[2 * b + 1], dst, s_done);
     } else {
       auto slot_at = [&](int t) { return t < d.NT ? load_slot(d, t, lane) : none; };
@@ -1121,10 +1154,15 @@ __global__ void __launch_bounds__(256, 1) k_sweep_cluster(SweepP<T> p) {
     if (prof) { tp1 = gtimer(); atomicAdd(&d.phase_ns[0], tp1 - tp0); }
     cluster_barrier();
     if (prof) { tp0 = gtimer(); atomicAdd(&d.phase_ns[1], tp0 - tp1); }
-    // phase B: the instance's bus tasks, two at a time per warp (warp-uniform loops)
+    // phase B: the instance's bus tasks, two at a time per warp, one in FP64 (warp-uniform loops)
     const ResDst dst = {&s_res[slot][0], nullptr, 1, slot, k};
-    if (RES) {
+    if (RES && sizeof(T) == 8 && nwc >= t1 - t0) {  // FP64, one task per warp
+      bus_task_one(d, task_load<T, false>(d, ta, nullptr), dst);
+    } else if (RES) {
       bus_task_pair(d, task_load<T, false>(d, ta, nullptr), task_load<T, false>(d, tb, nullptr), dst);
+    } else if (sizeof(T) == 8) {
+      for (int t = t0 + cw; t < t1; t += nwc)
+        bus_task_one(d, task_load<T, false>(d, task_static<T>(d, load_slot(d, t, lane)), nullptr), dst);
     } else {
       for (int t = t0 + cw; t < t1; t += 2 * nwc) {
         const Slot sa = load_slot(d, t, lane);
@@ -1531,12 +1569,17 @@ static acopf_status sweep_shape(Ctx& c, const SweepP<T>& p, SweepShape& sh) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<T, true>, threads, smem);
     if (c.ctas_per_sm > 0 && c.ctas_per_sm < per_sm) per_sm = c.ctas_per_sm;
+    const long cap = (long)per_sm * c.num_sms;
     const long wpb = threads / 32;
     long need = ((long)d.G + d.L + threads - 1) / threads;
     const long need_b = ((long)d.NT + 2 * wpb - 1) / (2 * wpb);
+    // the FP64 sweep gives each warp one bus task when the grid still fits
+    // (two interleaved FP64 tasks take about twice as long as one)
+    const long need_b1 = ((long)d.NT + wpb - 1) / wpb;
+    if (sizeof(T) == 8 && need_b1 > need && need_b1 <= cap) need = need_b1;
     if (need_b > need) need = need_b;
     if (need < 1) need = 1;
-    if (per_sm >= 1 && need <= (long)per_sm * c.num_sms) {
+    if (per_sm >= 1 && need <= cap) {
       sh = {(void*)k_sweep<T, true>, (int)need, smem};
       return ACOPF_OK;
     }
@@ -1562,7 +1605,8 @@ static acopf_status sweep_shape(Ctx& c, const SweepP<T>& p, SweepShape& sh) {
 
 // Cluster size of sweep_stages 4: enough CTAs for one thread per generator or
 // branch of the largest instance, at most 16, fewer when a cluster of that
-// size cannot be resident.
+// size cannot be resident.  The FP64 sweep takes one bus task per warp when a
+// resident cluster of at most 16 CTAs allows it (as in sweep_shape).
 template <typename T>
 static int cluster_size(Ctx& c, int threads, cudaLaunchConfig_t& cfg, cudaLaunchAttribute& attr, bool& res) {
   long items = 1, tasks = 0;
@@ -1581,6 +1625,14 @@ static int cluster_size(Ctx& c, int threads, cudaLaunchConfig_t& cfg, cudaLaunch
   if (cs > 16) cs = 16;
   void* fn = res ? (void*)k_sweep_cluster<T, true> : (void*)k_sweep_cluster<T, false>;
   cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  const long cs_b1 = (tasks + wpb - 1) / wpb;
+  if (sizeof(T) == 8 && res && cs_b1 > cs && cs_b1 <= 16) {
+    cfg.gridDim = dim3((unsigned)cs_b1);
+    attr.val.clusterDim.x = (unsigned)cs_b1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n >= 1) return (int)cs_b1;
+    cudaGetLastError();
+  }
   for (; cs > 1; --cs) {
     cfg.gridDim = dim3(cs);
     attr.val.clusterDim.x = cs;
