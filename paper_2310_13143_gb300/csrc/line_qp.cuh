@@ -5,6 +5,7 @@
 #pragma once
 
 #include <math.h>
+#include <string.h>
 
 #ifndef ACOPF_HD
 #define ACOPF_HD __host__ __device__
@@ -39,6 +40,74 @@ ACOPF_HD inline T clampv(T v, T lo, T hi) {
   return v < lo ? lo : (v > hi ? hi : v);
 }
 
+// FP64 <-> FP32 conversions in integer operations, from the IEEE 754
+// binary64 and binary32 formats.  On GB300 a conversion instruction with an
+// FP64 operand issues at the FP64 rate, a small fraction of the FP32 and
+// integer rates, and the FP64 line solve converts some fifty values per
+// branch for its FP32 predictor.
+ACOPF_HD inline unsigned long long bits_of(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long b;
+  memcpy(&b, &x, 8);
+  return b;
+#endif
+}
+ACOPF_HD inline double double_of(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double x;
+  memcpy(&x, &b, 8);
+  return x;
+#endif
+}
+ACOPF_HD inline float float_of(unsigned u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+#endif
+}
+ACOPF_HD inline unsigned bits_of(float f) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(f);
+#else
+  unsigned u;
+  memcpy(&u, &f, 4);
+  return u;
+#endif
+}
+// x rounded toward zero to FP32 (the 52-bit fraction cut to 23 bits);
+// magnitudes below the FP32 normal range give a signed zero, above it an
+// infinity; a NaN stays a NaN.  For values that seed or predict, where the
+// rounding does not matter.
+ACOPF_HD inline float f32_trunc(double x) {
+  const unsigned long long b = bits_of(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  unsigned out;
+  if (e <= 0) out = sign;
+  else if (e >= 255) out = sign | 0x7f800000u | (e == 2047 - 1023 + 127 && ((hi & 0xfffffu) | lo) ? 0x400000u : 0u);
+  else out = sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return float_of(out);
+}
+// f as FP64, exactly; an FP32 subnormal gives a signed zero
+ACOPF_HD inline double f64_widen(float f) {
+  const unsigned u = bits_of(f);
+  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xffu, frac = u & 0x7fffffu;
+  unsigned hi;
+  if (e == 0) hi = sign;
+  else if (e == 255) hi = sign | 0x7ff00000u | (frac >> 3);
+  else hi = sign | ((e - 127u + 1023u) << 20) | (frac >> 3);
+  const unsigned lo = e == 0 ? 0u : frac << 29;
+  return double_of(((unsigned long long)hi << 32) | lo);
+}
+
 // Quotient and reciprocal square root of the line and bus updates.  FP64
 // keeps the correctly rounded operations; the FP32 kernel takes the
 // special-function unit's approximations (__fdividef, rsqrtf: within a few
@@ -68,7 +137,9 @@ ACOPF_HD inline double rsqrt_newton(double a, double y0) {
 }
 ACOPF_HD inline double rsqrt_w(double a) {
 #ifdef __CUDA_ARCH__
-  if (a > 1e-30 && a < 1e30) return rsqrt_newton(a, (double)rsqrtf((float)a));
+  // a in [2^-99, 2^101): the FP32 estimate is in range (exponent test in
+  // integers, the conversions too; see f32_trunc)
+  if ((unsigned)(bits_of(a) >> 52) - (1023u - 99u) < 200u) return rsqrt_newton(a, f64_widen(rsqrtf(f32_trunc(a))));
 #endif
   return 1.0 / sqrt(a);
 }
@@ -742,40 +813,44 @@ ACOPF_HD inline void line_solve(const LineQP<T>& P, T x[4], T u[4], T beta, T al
 // predicts which bounds and rows are active;
 // the equality-constrained QP on that set is solved in FP64 (Cholesky of Q on
 // the free variables, then the rows' multipliers from the Schur complement
-// S = N Q^-1 N'); the KKT conditions are checked in FP64: the Lagrangian
-// stationary in the free variables, every free variable within its bounds,
-// every row satisfied, every multiplier of an active row or bound of the
-// right sign, each up to a tolerance of 1e-11 of the problem's scale.  Both solutions are the unique KKT point, so they agree
-// up to rounding.  Returns false when the prediction fails the check and two
-// corrections of the set; the caller then runs the FP64 dual active-set
-// method.  On entry x and u hold a starting point and multipliers.
+// S = N Q^-1 N', in closed form for up to two active rows); the KKT
+// conditions are checked in FP64: the Lagrangian stationary in the free
+// variables, every free variable within its bounds, every row satisfied,
+// every multiplier of an active row or bound of the right sign, each up to a
+// tolerance of 1e-11 of the problem's scale.  Both solutions are the unique
+// KKT point, so they agree up to rounding.  Returns false when the prediction
+// fails the check and two corrections of the set; the caller then runs the
+// FP64 dual active-set method.  On entry x and u hold a starting point and
+// multipliers.  FP64 instructions issue at a small fraction of the FP32 rate
+// on GB300, so the FP64 part is written to be short.
 ACOPF_HD inline bool line_solve_predicted(const LineQP<double>& P, double x[4], double u[4]) {
+  // the FP32 copy for the predictor (truncated: the prediction is checked in FP64)
   LineQP<float> F;
 #pragma unroll
-  for (int k = 0; k < 10; ++k) F.q[k] = (float)P.q[k];
+  for (int k = 0; k < 10; ++k) F.q[k] = f32_trunc(P.q[k]);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    F.c[i] = (float)P.c[i];
-    F.lo[i] = (float)P.lo[i];
-    F.hi[i] = (float)P.hi[i];
+    F.c[i] = f32_trunc(P.c[i]);
+    F.lo[i] = f32_trunc(P.lo[i]);
+    F.hi[i] = f32_trunc(P.hi[i]);
   }
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) F.R[r][i] = (float)P.R[r][i];
-    F.rb[r] = (float)P.rb[r];
+    for (int i = 0; i < 4; ++i) F.R[r][i] = f32_trunc(P.R[r][i]);
+    F.rb[r] = f32_trunc(P.rb[r]);
     F.on[r] = P.on[r];
   }
-  F.alo = (float)P.alo;
-  F.ahi = (float)P.ahi;
+  F.alo = f32_trunc(P.alo);
+  F.ahi = f32_trunc(P.ahi);
   F.ang = P.ang;
   // the FP32 augmented Lagrangian from the multipliers given and the
   // unconstrained start clamped into the box
   float xf[4], uf[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    xf[i] = clampv((float)x[i], F.lo[i], F.hi[i]);
-    uf[i] = (float)u[i];
+    xf[i] = clampv(f32_trunc(x[i]), F.lo[i], F.hi[i]);
+    uf[i] = f32_trunc(u[i]);
   }
   {
     const float qd = fmax(fmax(F.q[0], F.q[4]), fmax(F.q[7], F.q[9]));
@@ -819,7 +894,7 @@ ACOPF_HD inline bool line_solve_predicted(const LineQP<double>& P, double x[4], 
   for (int i = 0; i < 4; ++i) cmf = fmax(cmf, fabs(F.c[i]));
 #pragma unroll
   for (int k = 0; k < 10; ++k) qmf = fmax(qmf, fabs(F.q[k]));
-  const double cm = cmf, qm = qmf;
+  const double cm = f64_widen(cmf), qm = f64_widen(qmf);
   double xs[4], mu[4];
   bool ok = false;
   // the predicted set, then at most two corrections of it (bounds and rows
@@ -840,49 +915,129 @@ ACOPF_HD inline bool line_solve_predicted(const LineQP<double>& P, double x[4], 
       rhs[i] = ((fx >> i) & 1u) ? 0.0 : sv;
     }
     chol4_solve(fac, rhs, y);
-    // W_r = Q_FF^-1 n_r(F) for the active rows, S = N W, t = N y - (b - N xb)
-    double W[4][4], S[10], t[4];
+    // the multipliers of the active rows from the Schur complement S = N W,
+    // W = Q_FF^-1 N(F)', t = N y - (b - N xb) (N: the active rows, N(F) on
+    // the free variables); then xs = y - W' mu and gm = N' mu
+    double gm[4];
+    const int na = (int)(act & 1u) + (int)((act >> 1) & 1u) + (int)((act >> 2) & 1u) + (int)((act >> 3) & 1u);
+    if (na <= 2) {
+      // at most two active rows (the common case): S is 1x1 or 2x2, solved
+      // in closed form, and two row slots replace the four rows
+      int r0 = -1, r1 = -1;
 #pragma unroll
-    for (int k = 0; k < 10; ++k) S[k] = 0.0;
+      for (int r = 0; r < 4; ++r)
+        if ((act >> r) & 1u) {
+          if (r0 < 0) r0 = r;
+          else r1 = r;
+        }
+      double m0[4], m1[4], c0 = 0.0, c1 = 0.0;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      t[r] = 0.0;
+      for (int i = 0; i < 4; ++i) m0[i] = m1[i] = 0.0;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) W[r][i] = 0.0;
-      if (!((act >> r) & 1u)) continue;
-      double nf[4], bf = b[r];
+      for (int r = 0; r < 4; ++r) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (r == r0) m0[i] = n[r][i];
+          if (r == r1) m1[i] = n[r][i];
+        }
+        if (r == r0) c0 = b[r];
+        if (r == r1) c1 = b[r];
+      }
+      // on the free variables; the fixed ones go to the right-hand side
+      // (xb is 0 on the free variables)
+      double f0[4], f1[4], W0[4] = {0.0, 0.0, 0.0, 0.0}, W1[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const bool fixed = (fx >> i) & 1u;
-        nf[i] = fixed ? 0.0 : n[r][i];
-        if (fixed) bf -= n[r][i] * xb[i];
+        f0[i] = fixed ? 0.0 : m0[i];
+        f1[i] = fixed ? 0.0 : m1[i];
+        c0 -= m0[i] * xb[i];
+        c1 -= m1[i] * xb[i];
       }
-      chol4_solve(fac, nf, W[r]);
-      double ny = 0.0;
+      double mu0 = 0.0, mu1 = 0.0;
+      if (r0 >= 0) {
+        chol4_solve(fac, f0, W0);
+        double t0 = -c0, s00 = 0.0;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) ny += nf[i] * y[i];
-      t[r] = ny - bf;
-    }
+        for (int i = 0; i < 4; ++i) {
+          t0 += f0[i] * y[i];
+          s00 += f0[i] * W0[i];
+        }
+        if (!(s00 > 0.0)) return false;
+        if (r1 >= 0) {
+          chol4_solve(fac, f1, W1);
+          double t1 = -c1, s01 = 0.0, s11 = 0.0;
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int q = r; q < 4; ++q) {
-        if (!((act >> r) & 1u) || !((act >> q) & 1u)) continue;
-        double v = 0.0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) v += ((fx >> i) & 1u) ? 0.0 : n[r][i] * W[q][i];
-        S[pk(r, q)] = v;
+          for (int i = 0; i < 4; ++i) {
+            t1 += f1[i] * y[i];
+            s01 += f0[i] * W1[i];
+            s11 += f1[i] * W1[i];
+          }
+          const double det = s00 * s11 - s01 * s01;
+          if (!(det > 0.0)) return false;
+          const double id = 1.0 / det;
+          mu0 = (s11 * t0 - s01 * t1) * id;
+          mu1 = (s00 * t1 - s01 * t0) * id;
+        } else {
+          mu0 = t0 / s00;
+        }
       }
-    Chol4<double> fs;
-    if (!chol4_factor(S, act, fs)) return false;
-    chol4_solve(fs, t, mu);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      double v = ((fx >> i) & 1u) ? xb[i] : y[i];
+      for (int i = 0; i < 4; ++i) {
+        xs[i] = ((fx >> i) & 1u) ? xb[i] : y[i] - mu0 * W0[i] - mu1 * W1[i];
+        gm[i] = mu0 * m0[i] + mu1 * m1[i];
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) mu[r] = r == r0 ? mu0 : (r == r1 ? mu1 : 0.0);
+    } else {
+      // three or four active rows: S by a masked 4x4 Cholesky
+      double W[4][4], S[10], t[4];
+#pragma unroll
+      for (int k = 0; k < 10; ++k) S[k] = 0.0;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        t[r] = 0.0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) W[r][i] = 0.0;
+        if (!((act >> r) & 1u)) continue;
+        double nf[4], bf = b[r];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const bool fixed = (fx >> i) & 1u;
+          nf[i] = fixed ? 0.0 : n[r][i];
+          if (fixed) bf -= n[r][i] * xb[i];
+        }
+        chol4_solve(fac, nf, W[r]);
+        double ny = 0.0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ny += nf[i] * y[i];
+        t[r] = ny - bf;
+      }
 #pragma unroll
       for (int r = 0; r < 4; ++r)
-        if ((act >> r) & 1u) v -= mu[r] * W[r][i];
-      xs[i] = ((fx >> i) & 1u) ? xb[i] : v;
+#pragma unroll
+        for (int q = r; q < 4; ++q) {
+          if (!((act >> r) & 1u) || !((act >> q) & 1u)) continue;
+          double v = 0.0;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) v += ((fx >> i) & 1u) ? 0.0 : n[r][i] * W[q][i];
+          S[pk(r, q)] = v;
+        }
+      Chol4<double> fs;
+      if (!chol4_factor(S, act, fs)) return false;
+      chol4_solve(fs, t, mu);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        double v = ((fx >> i) & 1u) ? xb[i] : y[i];
+        gm[i] = 0.0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if ((act >> r) & 1u) {
+            v -= mu[r] * W[r][i];
+            gm[i] += mu[r] * n[r][i];
+          }
+        xs[i] = ((fx >> i) & 1u) ? xb[i] : v;
+      }
     }
     // KKT check: gradient of the Lagrangian g = Q x + c + sum_r mu_r n_r
     double g[4];
@@ -890,10 +1045,7 @@ ACOPF_HD inline bool line_solve_predicted(const LineQP<double>& P, double x[4], 
     double xm = 0.0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      g[i] += P.c[i];
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-        if ((act >> r) & 1u) g[i] += mu[r] * n[r][i];
+      g[i] += P.c[i] + gm[i];
       xm = fmax(xm, fabs(xs[i]));
     }
     const double tol = 1e-11 * (cm + qm * xm + 1.0), tx = 1e-11 * (xm + 1.0);
@@ -903,8 +1055,12 @@ ACOPF_HD inline bool line_solve_predicted(const LineQP<double>& P, double x[4], 
     for (int r = 0; r < 4; ++r) {
       if (!row_on(P, r)) continue;
       double v = -b[r];
+      if (r < 2) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) v += n[r][i] * xs[i];
+        for (int i = 0; i < 4; ++i) v += n[r][i] * xs[i];
+      } else {  // the angle rows: +-(x1 - x3), the same sums without the zero terms
+        v = r == 2 ? (v + xs[1]) - xs[3] : (v - xs[1]) + xs[3];
+      }
       const bool feas = v <= tx * (1.0 + fabs(b[r]));  // every row, active or not (a singular S shows here)
       if ((act >> r) & 1u) {
         if (!(mu[r] >= -tol)) { ok = false; nact &= ~(1u << r); }

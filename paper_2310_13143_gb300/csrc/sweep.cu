@@ -47,7 +47,24 @@ struct SweepP {
   int profile;    // accumulate CTA 0's phase times into d.phase_ns
   int smem_res;   // 1: residual maxima accumulated per CTA in shared memory (K <= kSmemResMax)
   int line_exact; // FP64 sweep: 1 = line subproblems by the exact dual active-set method, 0 = ALM
+  // the convergence test r <= eps && s <= eps_dual on the bit patterns of
+  // the residual maxima (non-negative doubles order as unsigned integers),
+  // so that it takes no FP64 instruction: can_stop = !fixed, both
+  // tolerances >= 0 (not NaN); their patterns (of +0 for -0)
+  int can_stop;
+  unsigned long long eps_bits, eps_dual_bits;
+  __device__ __forceinline__ bool converged(unsigned long long r, unsigned long long s) const {
+    return can_stop && r <= eps_bits && s <= eps_dual_bits;
+  }
 };
+
+template <typename T>
+static void set_stop_test(SweepP<T>& p) {
+  p.can_stop = !p.fixed && p.eps >= 0.0 && p.eps_dual >= 0.0;
+  const double e = p.eps + 0.0, ed = p.eps_dual + 0.0;
+  memcpy(&p.eps_bits, &e, 8);
+  memcpy(&p.eps_dual_bits, &ed, 8);
+}
 
 // instances up to which the residual maxima are accumulated in shared memory
 constexpr int kSmemResMax = 1024;
@@ -309,7 +326,6 @@ __device__ __forceinline__ void line_compute_to(const SweepP<T>& p, int l, const
   T x[4], u[4] = {uu.x, uu.y, uu.z, uu.w};
 #pragma unroll
   for (int i = 0; i < 4; ++i) x[i] = clampv(zv[i], P.lo[i], P.hi[i]);
-  const T beta = p.beta_scale * fmax(fmax(P.q[0], P.q[4]), fmax(P.q[7], P.q[9]));
   if constexpr (sizeof(T) == 8) {
     // FP64 sweep: the exact solution by default -- the active set predicted in
     // FP32 and the KKT point solved and checked in FP64, else the dual
@@ -327,9 +343,13 @@ __device__ __forceinline__ void line_compute_to(const SweepP<T>& p, int l, const
         }
       }
     }
-    if (alm) line_alm_call(P, x, u, beta, p.alm_tol, p.alm_outer, p.newton_max);
+    if (alm) {
+      const T beta = p.beta_scale * fmax(fmax(P.q[0], P.q[4]), fmax(P.q[7], P.q[9]));
+      line_alm_call(P, x, u, beta, p.alm_tol, p.alm_outer, p.newton_max);
+    }
   } else {
     // FP32 sweep: the augmented Lagrangian with refinement (Sec. IV-B)
+    const T beta = p.beta_scale * fmax(fmax(P.q[0], P.q[4]), fmax(P.q[7], P.q[9]));
     line_solve(P, x, u, beta, p.alm_tol, p.alm_outer, p.newton_max, nullptr, wset);
   }
   // flows at the solution (F and f0 read again)
@@ -377,7 +397,28 @@ struct ResDst {
   unsigned long long* slots;
   int K, slot;
   int kbase;  // instance of acc[0] (a cluster's one-instance accumulator; 0 otherwise)
+  // the maxima as the bit patterns of non-negative doubles (ordered as
+  // integers); positive values only
+  __device__ __forceinline__ void put_bits(int inst, unsigned long long r, unsigned long long s) const {
+    if (acc) {
+      if (r) atomicMax(&acc[inst - kbase], r);
+      if (s) atomicMax(&acc[K + inst - kbase], s);
+    } else {
+      if (r) atomicMax(&slots[(slot * 2 + 0) * K + inst], r);
+      if (s) atomicMax(&slots[(slot * 2 + 1) * K + inst], s);
+    }
+  }
+  // r, s >= 0 and not NaN.  In FP64 the test takes no FP64 comparison (an
+  // FP64 instruction issues at a small fraction of the FP32 rate on GB300):
+  // a positive double's pattern is a positive integer.  The FP32 overload
+  // widens with the conversion instruction and compares in FP64, which
+  // measured faster there than widening in integer operations.
   __device__ __forceinline__ void put(int inst, double r, double s) const {
+    const long long br = (long long)bits_of(r), bs = (long long)bits_of(s);
+    put_bits(inst, br > 0 ? (unsigned long long)br : 0ull, bs > 0 ? (unsigned long long)bs : 0ull);
+  }
+  __device__ __forceinline__ void put(int inst, float rf, float sf) const {
+    const double r = rf, s = sf;
     if (acc) {
       if (r > 0.0) atomicMax(&acc[inst - kbase], (unsigned long long)__double_as_longlong(r));
       if (s > 0.0) atomicMax(&acc[K + inst - kbase], (unsigned long long)__double_as_longlong(s));
@@ -420,7 +461,7 @@ __device__ __forceinline__ void res_max2(const ResDst& dst, T r, T s, int inst) 
   }
   int kprev = __shfl_up_sync(FULL, inst, 1);
   bool leader = (lane == 0 || kprev != inst) && inst >= 0;
-  if (leader) dst.put(inst, (double)r, (double)s);
+  if (leader) dst.put(inst, r, s);
 }
 
 // res_max2 for two tasks at once
@@ -446,8 +487,8 @@ __device__ __forceinline__ void res_max2_pair(const ResDst& dst, T ra, T sa, int
     }
   }
   const int kpa = __shfl_up_sync(FULL, ka, 1), kpb = __shfl_up_sync(FULL, kb, 1);
-  if ((lane == 0 || kpa != ka) && ka >= 0) dst.put(ka, (double)ra, (double)sa);
-  if ((lane == 0 || kpb != kb) && kb >= 0) dst.put(kb, (double)rb, (double)sb);
+  if ((lane == 0 || kpa != ka) && ka >= 0) dst.put(ka, ra, sa);
+  if ((lane == 0 || kpb != kb) && kb >= 0) dst.put(kb, rb, sb);
 }
 
 // ---------------------------------------------------------- bus update
@@ -501,9 +542,25 @@ __device__ __forceinline__ T over_r(T a, T r, T ir) {
   else return div_w(a, r);
 }
 
+// 1/r of a coupling's penalty, used by entry_sums and (FP64) entry_values:
+// the FP64 sweep takes the correctly rounded quotient once per coupling and
+// iteration (ir_once) and passes it to both; the FP32 sweep takes the
+// special-function quotient where entry_sums uses it (ir_at), as
+// entry_values does not need it
 template <typename T>
-__device__ __forceinline__ void entry_sums(int c, const V4<T>& x, const V4<T>& lm, T r, T* S) {
-  const T ir = div_w(T(1), r);
+__device__ __forceinline__ T ir_once(T r) {
+  if constexpr (sizeof(T) == 8) return div_w(T(1), r);
+  else return T(0);
+}
+template <typename T>
+__device__ __forceinline__ T ir_at(T r, T once) {
+  if constexpr (sizeof(T) == 8) return once;
+  else return div_w(T(1), r);
+}
+
+// ir = 1/r (see ir_once)
+template <typename T>
+__device__ __forceinline__ void entry_sums(int c, const V4<T>& x, const V4<T>& lm, T r, T ir, T* S) {
   S[0] += ir;
   if (c < 0) {
     S[1] += over_r(lm.x + r * x.x, r, ir);
@@ -563,9 +620,8 @@ __device__ __forceinline__ void entry_store(const Dev& d, int c, const V4<T>& zn
 // new bus-side value zn and multiplier ln of one coupling, with its residuals
 // (generator couplings in the x, y components, z and w zero)
 template <typename T>
-__device__ __forceinline__ void entry_values(int c, const V4<T>& x, const V4<T>& lm, const V4<T>& zo, T r, T n1, T n2,
-                                             T dw, T dth, T& rm, T& sm, V4<T>& zn, V4<T>& ln) {
-  const T ir = sizeof(T) == 8 ? div_w(T(1), r) : T(0);
+__device__ __forceinline__ void entry_values(int c, const V4<T>& x, const V4<T>& lm, const V4<T>& zo, T r, T ir, T n1,
+                                             T n2, T dw, T dth, T& rm, T& sm, V4<T>& zn, V4<T>& ln) {
   if (c < 0) {
     zn.x = over_r(lm.x + r * x.x - n1, r, ir);
     zn.y = over_r(lm.y + r * x.y - n2, r, ir);
@@ -595,9 +651,9 @@ __device__ __forceinline__ void entry_values(int c, const V4<T>& x, const V4<T>&
 
 template <typename T>
 __device__ __forceinline__ void entry_update(const Dev& d, int c, const V4<T>& x, const V4<T>& lm, const V4<T>& zo, T r,
-                                             T n1, T n2, T dw, T dth, T& rm, T& sm) {
+                                             T ir, T n1, T n2, T dw, T dth, T& rm, T& sm) {
   V4<T> zn, ln;
-  entry_values(c, x, lm, zo, r, n1, n2, dw, dth, rm, sm, zn, ln);
+  entry_values(c, x, lm, zo, r, ir, n1, n2, dw, dth, rm, sm, zn, ln);
   entry_store(d, c, zn, ln);
 }
 
@@ -712,8 +768,9 @@ __device__ __forceinline__ void bus_task_pair(const Dev& d, const TaskData<T>& a
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   T Sa[6] = {0, 0, 0, 0, 0, 0}, Sb[6] = {0, 0, 0, 0, 0, 0};
-  if (a.s.bus >= 0) entry_sums(a.s.code, a.x, a.lm, a.r, Sa);
-  if (b.s.bus >= 0) entry_sums(b.s.code, b.x, b.lm, b.r, Sb);
+  const T ira = ir_once(a.r), irb = ir_once(b.r);
+  if (a.s.bus >= 0) entry_sums(a.s.code, a.x, a.lm, a.r, ir_at(a.r, ira), Sa);
+  if (b.s.bus >= 0) entry_sums(b.s.code, b.x, b.lm, b.r, ir_at(b.r, irb), Sb);
   seg_scan2(a.s.bus, Sa, b.s.bus, Sb);
   T n1a = 0, n2a = 0, dwa = 0, dta = 0, n1b = 0, n2b = 0, dwb = 0, dtb = 0;
   if (a.last) bus_solve(d, a.s.bus, a.br, a.isref, Sa, n1a, n2a, dwa, dta);
@@ -730,12 +787,12 @@ __device__ __forceinline__ void bus_task_pair(const Dev& d, const TaskData<T>& a
   dtb = __shfl_sync(FULL, dtb, srcb);
   T rma = T(0), sma = T(0), rmb = T(0), smb = T(0);
   if (a.s.bus >= 0) {
-    entry_update(d, a.s.code, a.x, a.lm, a.zo, a.r, n1a, n2a, dwa, dta, rma, sma);
+    entry_update(d, a.s.code, a.x, a.lm, a.zo, a.r, ira, n1a, n2a, dwa, dta, rma, sma);
     if (!(rma == rma)) rma = T(1e30);
     if (!(sma == sma)) sma = T(1e30);
   }
   if (b.s.bus >= 0) {
-    entry_update(d, b.s.code, b.x, b.lm, b.zo, b.r, n1b, n2b, dwb, dtb, rmb, smb);
+    entry_update(d, b.s.code, b.x, b.lm, b.zo, b.r, irb, n1b, n2b, dwb, dtb, rmb, smb);
     if (!(rmb == rmb)) rmb = T(1e30);
     if (!(smb == smb)) smb = T(1e30);
   }
@@ -752,7 +809,8 @@ __device__ __forceinline__ void bus_task_one(const Dev& d, const TaskData<T>& a,
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   T S[6] = {0, 0, 0, 0, 0, 0};
-  if (a.s.bus >= 0) entry_sums(a.s.code, a.x, a.lm, a.r, S);
+  const T ir = ir_once(a.r);
+  if (a.s.bus >= 0) entry_sums(a.s.code, a.x, a.lm, a.r, ir_at(a.r, ir), S);
   seg_scan(a.s.bus, S);
   T n1 = 0, n2 = 0, dw = 0, dt = 0;
   if (a.last) bus_solve(d, a.s.bus, a.br, a.isref, S, n1, n2, dw, dt);
@@ -764,7 +822,7 @@ __device__ __forceinline__ void bus_task_one(const Dev& d, const TaskData<T>& a,
   dt = __shfl_sync(FULL, dt, src);
   T rm = T(0), sm = T(0);
   if (a.s.bus >= 0) {
-    entry_update(d, a.s.code, a.x, a.lm, a.zo, a.r, n1, n2, dw, dt, rm, sm);
+    entry_update(d, a.s.code, a.x, a.lm, a.zo, a.r, ir, n1, n2, dw, dt, rm, sm);
     if (!(rm == rm)) rm = T(1e30);
     if (!(sm == sm)) sm = T(1e30);
   }
@@ -789,7 +847,7 @@ __device__ void bus_task_big(const SweepP<T>& p, int q0, int q1, const ResDst& d
     T r;
     const int c = d.ent[q];
     entry_load(d, c, x, lm, zo, r);
-    entry_sums(c, x, lm, r, S);
+    entry_sums(c, x, lm, r, div_w(T(1), r), S);
   }
   seg_scan(bus, S);
   T n1 = 0, n2 = 0, dw = 0, dth = 0;
@@ -804,7 +862,7 @@ __device__ void bus_task_big(const SweepP<T>& p, int q0, int q1, const ResDst& d
     T r;
     const int c = d.ent[q];
     entry_load(d, c, x, lm, zo, r);
-    entry_update(d, c, x, lm, zo, r, n1, n2, dw, dth, rm, sm);
+    entry_update(d, c, x, lm, zo, r, div_w(T(1), r), n1, n2, dw, dth, rm, sm);
   }
   if (!(rm == rm)) rm = T(1e30);
   if (!(sm == sm)) sm = T(1e30);
@@ -1008,10 +1066,11 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && !RES) ? 2 : 1) k_sweep
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
       s_scale[k] = 1.0f;
       if (s_done[k]) continue;
-      double r = __longlong_as_double((long long)d.res_slots[(slot * 2 + 0) * K + k]);
-      double s = __longlong_as_double((long long)d.res_slots[(slot * 2 + 1) * K + k]);
-      bool conv = !p.fixed && r <= p.eps && s <= p.eps_dual;
+      const unsigned long long rbits = d.res_slots[(slot * 2 + 0) * K + k];
+      const unsigned long long sbits = d.res_slots[(slot * 2 + 1) * K + k];
+      const bool conv = p.converged(rbits, sbits);
       if (!conv && rb_now) {
+        const double r = __longlong_as_double((long long)rbits), s = __longlong_as_double((long long)sbits);
         float f = 1.0f;
         if (r > p.rb_mu * s) f = (float)p.rb_tau;
         else if (s > p.rb_mu * r) f = (float)(1.0 / p.rb_tau);
@@ -1024,8 +1083,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && !RES) ? 2 : 1) k_sweep
         if (blockIdx.x == 0) {
           d.admm_done[k] = 1;
           d.admm_iters[k] = it + 1;
-          d.admm_rs[k] = r;
-          d.admm_rs[K + k] = s;
+          d.admm_rs[k] = __longlong_as_double((long long)rbits);
+          d.admm_rs[K + k] = __longlong_as_double((long long)sbits);
         }
       } else {
         all = 0;
@@ -1188,10 +1247,9 @@ __global__ void __launch_bounds__(256, 1) k_sweep_cluster(SweepP<T> p) {
         sm = s2 > sm ? s2 : sm;
       }
       if (lane == 0) {
-        const double r = __longlong_as_double((long long)rm), s = __longlong_as_double((long long)sm);
-        s_rs[0] = r;
-        s_rs[1] = s;
-        s_stop = !p.fixed && r <= p.eps && s <= p.eps_dual;
+        s_rs[0] = __longlong_as_double((long long)rm);
+        s_rs[1] = __longlong_as_double((long long)sm);
+        s_stop = p.converged(rm, sm);
       }
     }
     __syncthreads();
@@ -1252,8 +1310,9 @@ __device__ __forceinline__ void bus_pair_dsm(DsmLane<T>& a, DsmLane<T>& b, const
   const int lane = threadIdx.x & 31;
   const bool ea = a.st.s.bus >= 0, eb = b.st.s.bus >= 0;
   T Sa[6] = {0, 0, 0, 0, 0, 0}, Sb[6] = {0, 0, 0, 0, 0, 0};
-  if (ea) entry_sums(a.st.s.code, xa, a.lm, a.r, Sa);
-  if (eb) entry_sums(b.st.s.code, xb, b.lm, b.r, Sb);
+  const T ira = ir_once(a.r), irb = ir_once(b.r);
+  if (ea) entry_sums(a.st.s.code, xa, a.lm, a.r, ir_at(a.r, ira), Sa);
+  if (eb) entry_sums(b.st.s.code, xb, b.lm, b.r, ir_at(b.r, irb), Sb);
   seg_scan2(a.st.s.bus, Sa, b.st.s.bus, Sb);
   T n1a = 0, n2a = 0, dwa = 0, dta = 0, n1b = 0, n2b = 0, dwb = 0, dtb = 0;
   if (a.st.last) {
@@ -1279,7 +1338,7 @@ __device__ __forceinline__ void bus_pair_dsm(DsmLane<T>& a, DsmLane<T>& b, const
   T rma = T(0), sma = T(0), rmb = T(0), smb = T(0);
   if (ea) {
     V4<T> zn, ln;
-    entry_values(a.st.s.code, xa, a.lm, a.zo, a.r, n1a, n2a, dwa, dta, rma, sma, zn, ln);
+    entry_values(a.st.s.code, xa, a.lm, a.zo, a.r, ira, n1a, n2a, dwa, dta, rma, sma, zn, ln);
     st_cluster(a.to, zn);
     st_cluster(a.to + sizeof(V4<T>), ln);
     a.zo = zn;
@@ -1289,7 +1348,7 @@ __device__ __forceinline__ void bus_pair_dsm(DsmLane<T>& a, DsmLane<T>& b, const
   }
   if (eb) {
     V4<T> zn, ln;
-    entry_values(b.st.s.code, xb, b.lm, b.zo, b.r, n1b, n2b, dwb, dtb, rmb, smb, zn, ln);
+    entry_values(b.st.s.code, xb, b.lm, b.zo, b.r, irb, n1b, n2b, dwb, dtb, rmb, smb, zn, ln);
     st_cluster(b.to, zn);
     st_cluster(b.to + sizeof(V4<T>), ln);
     b.zo = zn;
@@ -1435,10 +1494,9 @@ __global__ void __launch_bounds__(256, 1) k_sweep_cluster_dsm(SweepP<T> p) {
         sm = s2 > sm ? s2 : sm;
       }
       if (lane == 0) {
-        const double r = __longlong_as_double((long long)rm), s = __longlong_as_double((long long)sm);
-        s_rs[0] = r;
-        s_rs[1] = s;
-        s_stop = !p.fixed && r <= p.eps && s <= p.eps_dual;
+        s_rs[0] = __longlong_as_double((long long)rm);
+        s_rs[1] = __longlong_as_double((long long)sm);
+        s_stop = p.converged(rm, sm);
       }
     }
     __syncthreads();
@@ -1741,6 +1799,7 @@ static acopf_status run_sweep(Ctx& c, const admm_options& o, int fixed_iters) {
   p.profile = c.profiling ? 1 : 0;
   p.smem_res = d.K <= kSmemResMax;
   p.line_exact = o.line_solver == 0;
+  set_stop_test(p);
   const int threads = c.block_threads;
   if (c.sweep_stages == 4 && p.rb_period == 0) return run_sweep_cluster(c, p);
   SweepShape sh;
@@ -1864,6 +1923,7 @@ acopf_status run_sweep_static(Ctx& c, const admm_options& o, int n, double* rs, 
   p.profile = 0;  // not timed: acopf_profile covers the handle's own sweeps only
   p.smem_res = d.K <= kSmemResMax;
   p.line_exact = o.line_solver == 0;
+  set_stop_test(p);
   const int threads = c.block_threads;
   SweepShape sh;
   acopf_status st = sweep_shape(c, p, sh);

@@ -11,6 +11,14 @@ using namespace acopf;
 
 extern "C" double host_rsqrt_newton(double a, double y0) { return rsqrt_newton(a, y0); }
 
+// the integer FP64 <-> FP32 conversions, elementwise
+extern "C" void host_f32_trunc(int n, const double* x, float* out) {
+  for (int i = 0; i < n; ++i) out[i] = f32_trunc(x[i]);
+}
+extern "C" void host_f64_widen(int n, const float* x, double* out) {
+  for (int i = 0; i < n; ++i) out[i] = f64_widen(x[i]);
+}
+
 // in: q10 c4 lo4 hi4 R8 rb2 on2 alo ahi ang x4 (41 values per problem)
 static LineQP<double> make(const double* in) {
   LineQP<double> P;

@@ -4,6 +4,9 @@ the device header (tests/host/line_helpers.cpp):
 * the FP64 reciprocal square root by two Newton-Raphson steps from an FP32
   estimate meets its error bound (an estimate with relative error up to 2^-21
   ends within a few units in the last place of 1/sqrt(a));
+* the FP64 -> FP32 truncation and the FP32 -> FP64 widening in integer
+  operations (IEEE 754 binary64 and binary32) agree with numpy's
+  conversions: rounding toward zero, and exact widening;
 * the exact FP64 line solve by a predicted active set (eq. line_kernel: a
   strictly convex 4-variable QP with box, two line-limit rows and the angle
   rows) returns the same KKT point as the dual active-set method of Goldfarb
@@ -46,6 +49,44 @@ def test_rsqrt_newton_error_bound(lib):
             y = lib.host_rsqrt_newton(float(v), ref * (1.0 + e0))
             worst = max(worst, abs(y - ref) / ref)
     assert worst <= 4 * 2.0 ** -53, worst
+
+
+def test_integer_float_conversions(lib):
+    FP = C.POINTER(C.c_float)
+    rng = np.random.default_rng(3)
+    x = np.concatenate([
+        rng.standard_normal(3000) * np.exp(rng.uniform(-80, 80, 3000)),  # across the FP32 range
+        rng.standard_normal(200),
+        [0.0, -0.0, 1.0, -1.0, 1e30, -1e30, 3.4028234663852886e38, 1e-40, -1e-40, 1e39, -1e39, np.inf, -np.inf,
+         np.nan, 2.0 ** -126, 2.0 ** -127],
+    ])
+    out = np.zeros(len(x), dtype=np.float32)
+    lib.host_f32_trunc(len(x), np.ascontiguousarray(x).ctypes.data_as(DP), out.ctypes.data_as(FP))
+    # numpy rounds to nearest; step toward zero where that overshot |x|
+    with np.errstate(over="ignore"):
+        want = x.astype(np.float32)
+    over = np.isfinite(x) & (np.abs(want.astype(np.float64)) > np.abs(x))
+    want[over] = np.nextafter(want[over], np.float32(0))
+    tiny = np.isfinite(x) & (np.abs(x) < 2.0 ** -126)  # below the FP32 normal range: a signed zero
+    want[tiny] = np.copysign(np.float32(0), x[tiny]).astype(np.float32)
+    big = np.isfinite(x) & (np.abs(x) >= 2.0 ** 128)  # above it: an infinity
+    want[big] = np.copysign(np.float32(np.inf), x[big]).astype(np.float32)
+    nan = np.isnan(x)
+    assert np.isnan(out[nan]).all()
+    np.testing.assert_array_equal(out[~nan], want[~nan])
+    assert (np.signbit(out[~nan]) == np.signbit(x[~nan])).all()
+    # widening: exact for normal numbers, zeros and infinities; FP32 subnormals give a signed zero
+    f = np.concatenate([out[np.isfinite(out)], np.array([1e-40, -1e-40, np.inf, -np.inf, np.nan], dtype=np.float32)])
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    w = np.zeros(len(f))
+    lib.host_f64_widen(len(f), f.ctypes.data_as(FP), w.ctypes.data_as(DP))
+    ref = f.astype(np.float64)
+    sub = np.isfinite(ref) & (np.abs(ref) < 2.0 ** -126)
+    ref[sub] = np.copysign(0.0, ref[sub])
+    fn = np.isnan(f)
+    assert np.isnan(w[fn]).all()
+    np.testing.assert_array_equal(w[~fn], ref[~fn])
+    assert (np.signbit(w[~fn]) == np.signbit(ref[~fn])).all()
 
 
 def _random_problems(rng, n):
