@@ -441,6 +441,34 @@ __device__ __forceinline__ void res_flush(const ResDst& o) {
   }
 }
 
+// Residual maxima.  FP64 takes them on the bit patterns as integers, which
+// order non-negative doubles alike; a NaN's pattern (sign cleared) exceeds
+// every other, so a NaN component always reaches the test.  FP32 uses fmax,
+// which passes over a NaN component (a non-finite state is then caught by
+// the SQP's finiteness checks).
+//   rmax: max of two residuals (non-negative or NaN)
+//   amax: max(|a|, |b|)
+//   nan_big: a NaN residual as 1e30, so that the test cannot pass on it
+template <typename T>
+__device__ __forceinline__ T rmax(T a, T b) {
+  if constexpr (sizeof(T) == 8) {
+    const unsigned long long x = bits_of(a) & 0x7fffffffffffffffull, y = bits_of(b) & 0x7fffffffffffffffull;
+    return double_of(x > y ? x : y);
+  } else {
+    return fmax(a, b);
+  }
+}
+template <typename T>
+__device__ __forceinline__ T amax(T a, T b) {
+  if constexpr (sizeof(T) == 8) return rmax(a, b);
+  else return fmax(fabs(a), fabs(b));
+}
+template <typename T>
+__device__ __forceinline__ T nan_big(T v) {
+  if constexpr (sizeof(T) == 8) return (bits_of(v) & 0x7fffffffffffffffull) > 0x7ff0000000000000ull ? T(1e30) : v;
+  else return v == v ? v : T(1e30);
+}
+
 // Warp-level max of the residuals over runs of lanes that hold the same
 // instance (buses are sorted by instance, so runs are contiguous): a segmented
 // shuffle-down reduction in the sweep precision, then one 64-bit atomicMax per
@@ -455,8 +483,8 @@ __device__ __forceinline__ void res_max2(const ResDst& dst, T r, T s, int inst) 
     T s2 = __shfl_down_sync(FULL, s, o);
     int k2 = __shfl_down_sync(FULL, inst, o);
     if (lane + o < 32 && k2 == inst) {
-      r = fmax(r, r2);
-      s = fmax(s, s2);
+      r = rmax(r, r2);
+      s = rmax(s, s2);
     }
   }
   int kprev = __shfl_up_sync(FULL, inst, 1);
@@ -478,12 +506,12 @@ __device__ __forceinline__ void res_max2_pair(const ResDst& dst, T ra, T sa, int
     T sb2 = __shfl_down_sync(FULL, sb, o);
     int kb2 = __shfl_down_sync(FULL, kb, o);
     if (lane + o < 32 && ka2 == ka) {
-      ra = fmax(ra, ra2);
-      sa = fmax(sa, sa2);
+      ra = rmax(ra, ra2);
+      sa = rmax(sa, sa2);
     }
     if (lane + o < 32 && kb2 == kb) {
-      rb = fmax(rb, rb2);
-      sb = fmax(sb, sb2);
+      rb = rmax(rb, rb2);
+      sb = rmax(sb, sb2);
     }
   }
   const int kpa = __shfl_up_sync(FULL, ka, 1), kpb = __shfl_up_sync(FULL, kb, 1);
@@ -626,9 +654,9 @@ __device__ __forceinline__ void entry_values(int c, const V4<T>& x, const V4<T>&
     zn.x = over_r(lm.x + r * x.x - n1, r, ir);
     zn.y = over_r(lm.y + r * x.y - n2, r, ir);
     zn.z = zn.w = T(0);
-    sm = fmax(sm, r * fmax(fabs(zn.x - zo.x), fabs(zn.y - zo.y)));
+    sm = rmax(sm, r * amax(zn.x - zo.x, zn.y - zo.y));
     const T rx = x.x - zn.x, ry = x.y - zn.y;
-    rm = fmax(rm, fmax(fabs(rx), fabs(ry)));
+    rm = rmax(rm, amax(rx, ry));
     ln.x = lm.x + r * rx;
     ln.y = lm.y + r * ry;
     ln.z = ln.w = T(0);
@@ -637,11 +665,11 @@ __device__ __forceinline__ void entry_values(int c, const V4<T>& x, const V4<T>&
     zn.y = over_r(lm.y + r * x.y + n2, r, ir);
     zn.z = dw;
     zn.w = dth;
-    const T a1 = fmax(fabs(zn.x - zo.x), fabs(zn.y - zo.y));
-    const T a2 = fmax(fabs(zn.z - zo.z), fabs(zn.w - zo.w));
-    sm = fmax(sm, r * fmax(a1, a2));
+    const T a1 = amax(zn.x - zo.x, zn.y - zo.y);
+    const T a2 = amax(zn.z - zo.z, zn.w - zo.w);
+    sm = rmax(sm, r * rmax(a1, a2));
     const T rx = x.x - zn.x, ry = x.y - zn.y, rw = x.z - zn.z, rt = x.w - zn.w;
-    rm = fmax(rm, fmax(fmax(fabs(rx), fabs(ry)), fmax(fabs(rw), fabs(rt))));
+    rm = rmax(rm, rmax(amax(rx, ry), amax(rw, rt)));
     ln.x = lm.x + r * rx;
     ln.y = lm.y + r * ry;
     ln.z = lm.z + r * rw;
@@ -788,13 +816,13 @@ __device__ __forceinline__ void bus_task_pair(const Dev& d, const TaskData<T>& a
   T rma = T(0), sma = T(0), rmb = T(0), smb = T(0);
   if (a.s.bus >= 0) {
     entry_update(d, a.s.code, a.x, a.lm, a.zo, a.r, ira, n1a, n2a, dwa, dta, rma, sma);
-    if (!(rma == rma)) rma = T(1e30);
-    if (!(sma == sma)) sma = T(1e30);
+    rma = nan_big(rma);
+    sma = nan_big(sma);
   }
   if (b.s.bus >= 0) {
     entry_update(d, b.s.code, b.x, b.lm, b.zo, b.r, irb, n1b, n2b, dwb, dtb, rmb, smb);
-    if (!(rmb == rmb)) rmb = T(1e30);
-    if (!(smb == smb)) smb = T(1e30);
+    rmb = nan_big(rmb);
+    smb = nan_big(smb);
   }
   res_max2_pair(dst, rma, sma, a.s.inst, rmb, smb, b.s.inst);
 }
@@ -823,8 +851,8 @@ __device__ __forceinline__ void bus_task_one(const Dev& d, const TaskData<T>& a,
   T rm = T(0), sm = T(0);
   if (a.s.bus >= 0) {
     entry_update(d, a.s.code, a.x, a.lm, a.zo, a.r, ir, n1, n2, dw, dt, rm, sm);
-    if (!(rm == rm)) rm = T(1e30);
-    if (!(sm == sm)) sm = T(1e30);
+    rm = nan_big(rm);
+    sm = nan_big(sm);
   }
   res_max2(dst, rm, sm, a.s.inst);
 }
@@ -864,8 +892,8 @@ __device__ void bus_task_big(const SweepP<T>& p, int q0, int q1, const ResDst& d
     entry_load(d, c, x, lm, zo, r);
     entry_update(d, c, x, lm, zo, r, div_w(T(1), r), n1, n2, dw, dth, rm, sm);
   }
-  if (!(rm == rm)) rm = T(1e30);
-  if (!(sm == sm)) sm = T(1e30);
+  rm = nan_big(rm);
+  sm = nan_big(sm);
   res_max2(dst, rm, sm, inst);
 }
 
@@ -1343,8 +1371,8 @@ __device__ __forceinline__ void bus_pair_dsm(DsmLane<T>& a, DsmLane<T>& b, const
     st_cluster(a.to + sizeof(V4<T>), ln);
     a.zo = zn;
     a.lm = ln;
-    if (!(rma == rma)) rma = T(1e30);
-    if (!(sma == sma)) sma = T(1e30);
+    rma = nan_big(rma);
+    sma = nan_big(sma);
   }
   if (eb) {
     V4<T> zn, ln;
@@ -1353,8 +1381,8 @@ __device__ __forceinline__ void bus_pair_dsm(DsmLane<T>& a, DsmLane<T>& b, const
     st_cluster(b.to + sizeof(V4<T>), ln);
     b.zo = zn;
     b.lm = ln;
-    if (!(rmb == rmb)) rmb = T(1e30);
-    if (!(smb == smb)) smb = T(1e30);
+    rmb = nan_big(rmb);
+    smb = nan_big(smb);
   }
   res_max2_pair(dst, rma, sma, a.st.s.inst, rmb, smb, b.st.s.inst);
 }
