@@ -122,18 +122,19 @@ ACOPF_HD inline float div_w(float a, float b) {
   return a / b;
 #endif
 }
-// 1/sqrt(a) in FP64 from an estimate y0 refined by two Newton-Raphson steps
-// on f(y) = 1/y^2 - a:  y <- y (3 - a y^2) / 2.  A relative error e becomes
-// about -3/2 e^2 per step, so an FP32 estimate (|e| <= 2^-21) ends below
-// FP64 rounding after two steps.  On the device the estimate is the FP32
-// special-function unit's rsqrtf; a correctly rounded square root and
-// division cost many FP64 instructions on GB300, whose FP64 rate is a small
-// fraction of FP32.
+// 1/sqrt(a) in FP64 from an estimate y0 by one third-order step: with
+// e = 1 - a y0^2 the exact value is y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8
+// + 5e^3/16 + ...), and the step keeps the series to e^2.  A relative error d
+// of y0 leaves about 5/2 d^3, so an FP32 estimate (|d| <= 2^-21) ends below
+// FP64 rounding: five FP64 instructions, against eight for two Newton-Raphson
+// steps.  On the device the estimate is the FP32 special-function unit's
+// rsqrtf; a correctly rounded square root and division cost many FP64
+// instructions on GB300, whose FP64 rate is a small fraction of FP32.
 ACOPF_HD inline double rsqrt_newton(double a, double y0) {
-  double y = y0;
-  y = y * (1.5 - 0.5 * a * y * y);
-  y = y * (1.5 - 0.5 * a * y * y);
-  return y;
+  const double t = a * y0;
+  const double e = fma(-t, y0, 1.0);
+  const double q = e * fma(0.375, e, 0.5);
+  return fma(y0, q, y0);
 }
 ACOPF_HD inline double rsqrt_w(double a) {
 #ifdef __CUDA_ARCH__
@@ -143,6 +144,12 @@ ACOPF_HD inline double rsqrt_w(double a) {
 #endif
   return 1.0 / sqrt(a);
 }
+// a > 0, false for a NaN; in FP64 on the bit pattern (no FP64 comparison)
+ACOPF_HD inline bool pos_w(double a) {
+  const long long b = (long long)bits_of(a);
+  return b > 0 && b <= 0x7ff0000000000000LL;
+}
+ACOPF_HD inline bool pos_w(float a) { return a > 0.f; }
 ACOPF_HD inline float rsqrt_w(float a) {
 #ifdef __CUDA_ARCH__
   return rsqrtf(a);
@@ -202,19 +209,19 @@ ACOPF_HD inline bool chol4_factor(const T h[10], unsigned fr, Chol4<T>& f) {
   T a00 = f0 ? h[0] : T(1), a11 = f1 ? h[4] : T(1), a22 = f2 ? h[7] : T(1), a33 = f3 ? h[9] : T(1);
   T a01 = f0 && f1 ? h[1] : T(0), a02 = f0 && f2 ? h[2] : T(0), a03 = f0 && f3 ? h[3] : T(0);
   T a12 = f1 && f2 ? h[5] : T(0), a13 = f1 && f3 ? h[6] : T(0), a23 = f2 && f3 ? h[8] : T(0);
-  if (!(a00 > T(0))) return false;
+  if (!pos_w(a00)) return false;
   f.i00 = rsqrt_w(a00);
   f.l10 = a01 * f.i00; f.l20 = a02 * f.i00; f.l30 = a03 * f.i00;
   T d1 = a11 - f.l10 * f.l10;
-  if (!(d1 > T(0))) return false;
+  if (!pos_w(d1)) return false;
   f.i11 = rsqrt_w(d1);
   f.l21 = (a12 - f.l20 * f.l10) * f.i11; f.l31 = (a13 - f.l30 * f.l10) * f.i11;
   T d2 = a22 - f.l20 * f.l20 - f.l21 * f.l21;
-  if (!(d2 > T(0))) return false;
+  if (!pos_w(d2)) return false;
   f.i22 = rsqrt_w(d2);
   f.l32 = (a23 - f.l30 * f.l20 - f.l31 * f.l21) * f.i22;
   T d3 = a33 - f.l30 * f.l30 - f.l31 * f.l31 - f.l32 * f.l32;
-  if (!(d3 > T(0))) return false;
+  if (!pos_w(d3)) return false;
   f.i33 = rsqrt_w(d3);
   return true;
 }
@@ -1042,12 +1049,14 @@ ACOPF_HD inline bool line_solve_predicted(const LineQP<double>& P, double x[4], 
     // KKT check: gradient of the Lagrangian g = Q x + c + sum_r mu_r n_r
     double g[4];
     symv4(P.q, xs, g);
-    double xm = 0.0;
+    unsigned long long xmb = 0ull;  // max |xs_i| on the bit patterns (a NaN the largest)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       g[i] += P.c[i] + gm[i];
-      xm = fmax(xm, fabs(xs[i]));
+      const unsigned long long b = bits_of(xs[i]) & 0x7fffffffffffffffull;
+      xmb = b > xmb ? b : xmb;
     }
+    const double xm = double_of(xmb);
     const double tol = 1e-11 * (cm + qm * xm + 1.0), tx = 1e-11 * (xm + 1.0);
     unsigned nfx = fx, nhs = hs, nact = act;
     ok = true;
@@ -1089,7 +1098,7 @@ ACOPF_HD inline bool line_solve_predicted(const LineQP<double>& P, double x[4], 
 #pragma unroll
   for (int i = 0; i < 4; ++i) x[i] = clampv(xs[i], P.lo[i], P.hi[i]);
 #pragma unroll
-  for (int r = 0; r < 4; ++r) u[r] = ((act >> r) & 1u) && mu[r] > 0.0 ? mu[r] : 0.0;
+  for (int r = 0; r < 4; ++r) u[r] = ((act >> r) & 1u) && pos_w(mu[r]) ? mu[r] : 0.0;
   return true;
 }
 
