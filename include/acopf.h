@@ -365,7 +365,10 @@ acopf_status acopf_get_profile_phases(acopf_handle h, double* ns);
  * for one thread per generator or branch of the largest instance), whose
  * barriers are the cluster's hardware barrier and whose residual maxima are
  * combined in distributed shared memory, so instances never wait on one
- * another (residual balancing off -- otherwise as with 0). */
+ * another (residual balancing off -- otherwise as with 0).  With 3 and 4 the
+ * FP64 sweep sizes the grid (or cluster) for one bus task per warp where it
+ * still fits: FP64 arithmetic issues at a small fraction of the FP32 rate,
+ * so two tasks interleaved in a warp take twice as long as one. */
 acopf_status acopf_tune(acopf_handle h, int32_t block_threads, int32_t ctas_per_sm, int32_t sweep_stages);
 
 /* Autotuner of the sweep's launch shape.  If cache_path (may be NULL) names a
