@@ -1,6 +1,6 @@
 // Host build of the line subproblem's numerical helpers, for the CPU tests:
-// the FP64 reciprocal square root by Newton-Raphson steps from a given
-// estimate, and the exact FP64 line solve by a predicted active set against
+// the FP64 reciprocal square root by one third-order step from a given
+// estimate, the integer FP64 <-> FP32 conversions, and the exact FP64 line solve by a predicted active set against
 // the dual active-set method.  Plain C entry points for ctypes.
 #define ACOPF_HD
 #include <math.h>

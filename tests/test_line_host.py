@@ -1,7 +1,7 @@
 """CPU tests of the line subproblem's numerical helpers, from a host build of
 the device header (tests/host/line_helpers.cpp):
 
-* the FP64 reciprocal square root by two Newton-Raphson steps from an FP32
+* the FP64 reciprocal square root by one third-order step from an FP32
   estimate meets its error bound (an estimate with relative error up to 2^-21
   ends within a few units in the last place of 1/sqrt(a));
 * the FP64 -> FP32 truncation and the FP32 -> FP64 widening in integer
